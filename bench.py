@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Hamming decoder.
+
+Default workload (one "step"): the single-n sweep -- Hamming (15,11), (31,26)
+and (63,57), 2^24 codewords each, packed LSB-first uint32 streams of encoded
+uniform data with single-bit errors (p1 = 0.1) and double-bit errors
+(p2 = 0.01), u8 syndromes and an error count.  A step decodes all three
+streams (one hd_decode call each).  Inputs are resident in HBM before the
+timed region; the three streams and their outputs (475 MB) are larger than
+L2 and each buffer is touched once per step.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (the reference arm of this workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEP_CODES = (15, 31, 63)
+SWEEP_N = 1 << 24
+SWEEP_P1, SWEEP_P2 = 0.1, 0.01
+ROOFLINE_N = 63  # the dominant kernel of a sweep step (largest byte count)
+METRIC = "decoded Gbit/s"
+WORKLOAD = ("single-n sweep: Hamming (15,11), (31,26), (63,57); 2^24 codewords each; packed LSB-first "
+            "uint32 streams; encoded uniform data (seed n), single-bit error p1=0.1 and double-bit p2=0.01 "
+            "per codeword; u8 syndromes + err_count")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    return ap.parse_args()
+
+
+def code_params(n):
+    m = (n + 1).bit_length() - 1
+    return m, n - m
+
+
+def algorithmic_bytes(n, N, syn_bytes=1):
+    """Bytes one decode must move: n/8 read + k/8 written + syndromes per codeword."""
+    m, k = code_params(n)
+    return (N * n + 7) // 8 + (N * k + 7) // 8 + N * syn_bytes
+
+
+def dist_setup(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != gpus:
+        if world == 1 and gpus > 1:
+            raise SystemExit("--gpus N > 1 must be launched with torch.distributed.run (one rank per GPU)")
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None, interval_ms: int = 20):
+        self.uuid = (uuid or "").lower().replace("gpu-", "").replace("-", "")
+        self.tmp = tempfile.NamedTemporaryFile(prefix="hdclk", suffix=".csv", delete=False)
+        self.proc = None
+        self.interval_ms = interval_ms
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", str(self.interval_ms)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.close()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.tmp.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    u = parts[0].lower().replace("gpu-", "").replace("-", "")
+                    if self.uuid and u != self.uuid:
+                        continue
+                    rows.append(parts)
+        finally:
+            os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # samples under load: the upper half of the SM clock distribution
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": float(np.median(sm_sorted[len(sm_sorted) // 2:])) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_inputs(codes, per_code):
+    import oracle
+    from paper_1412_6862_gb300 import synth
+    out = {}
+    for n in codes:
+        m, k = code_params(n)
+        N = per_code[n]
+        data = synth.random_words(n, N * k)
+        s = oracle.encode(data, n, N)
+        synth.apply_errors(s, synth.error_events(n, n, N, p1=SWEEP_P1, p2=SWEEP_P2))
+        out[n] = s
+    return out
+
+
+def oracle_decode_all(streams, per_code, threads):
+    import oracle
+    bits = 0
+    for n, s in streams.items():
+        m, k = code_params(n)
+        N = per_code[n]
+        outb = np.zeros((N * k + 31) // 32, np.uint32)
+        syn = np.zeros(N, np.uint8)
+        oracle.decode_threaded(s, n, N, oracle.SYN_U8, threads, outb, syn)
+        bits += N * k
+    return bits
+
+
+def calibrate_oracle(threads, seconds):
+    """Codewords per code so that one pass over the three codes takes ~seconds."""
+    probe = {n: 1 << 15 for n in SWEEP_CODES}
+    streams = oracle_sample_inputs(SWEEP_CODES, probe)
+    t0 = time.perf_counter()
+    oracle_decode_all(streams, probe, threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    scale = seconds / dt
+    return {n: int(max(1 << 12, min(SWEEP_N, (probe[n] * scale) // 32 * 32))) for n in SWEEP_CODES}
+
+
+def cpu_baseline(seconds):
+    threads = os.cpu_count() or 1
+    per_code = calibrate_oracle(threads, seconds)
+    streams = oracle_sample_inputs(SWEEP_CODES, per_code)
+    t0 = time.perf_counter()
+    bits = oracle_decode_all(streams, per_code, threads)
+    dt = time.perf_counter() - t0
+    return {"value": bits / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {per_code[15]}/{per_code[31]}/{per_code[63]} codewords of the (15,11)/(31,26)/(63,57) "
+                      f"streams, bit-by-bit C oracle on {threads} host threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    # a step decodes a bounded sample of each stream; the whole run stays within minutes
+    budget = min(6.0, 150.0 / max(1, args.steps + args.warmup))
+    per_code = calibrate_oracle(threads, budget)
+    streams = oracle_sample_inputs(SWEEP_CODES, per_code)
+    for _ in range(args.warmup):
+        oracle_decode_all(streams, per_code, threads)
+    t0 = time.perf_counter()
+    bits = 0
+    for _ in range(args.steps):
+        bits += oracle_decode_all(streams, per_code, threads)
+    dt = time.perf_counter() - t0
+    value = bits / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / max(1, args.steps) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_codewords": per_code},
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_code} codewords per stream per step, bit-by-bit C oracle"},
+            "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1412_6862_gb300 import build as hd_build
+    hd_build.build()
+    from paper_1412_6862_gb300 import hd, synth
+
+    stream_h = torch.cuda.current_stream(dev)
+    sh = int(stream_h.cuda_stream)
+    bufs = {}
+    for n in SWEEP_CODES:
+        m, k = code_params(n)
+        N = SWEEP_N
+        seed = n + 1000 * rank
+        data = synth.random_words(seed, N * k)
+        d_data = torch.from_numpy(data.view(np.int32)).to(dev)
+        d_in = hd.encode(d_data, n, N)                      # GPU encoder builds the codewords
+        host = d_in.cpu().numpy().view(np.uint32).copy()
+        synth.apply_errors(host, synth.error_events(seed, n, N, p1=SWEEP_P1, p2=SWEEP_P2))
+        pinned = torch.from_numpy(host.view(np.int32)).pin_memory()
+        d_in.copy_(pinned)
+        del d_data
+        out = torch.empty(hd.words_for(N * k), dtype=torch.int32, device=dev)
+        syn = torch.empty(N, dtype=torch.uint8, device=dev)
+        err = torch.empty(1, dtype=torch.int64, device=dev)
+        out_h = torch.empty_like(out, device="cpu").pin_memory()
+        syn_h = torch.empty_like(syn, device="cpu").pin_memory()
+        err_h = torch.empty_like(err, device="cpu").pin_memory()
+        bufs[n] = dict(N=N, k=k, d_in=d_in, pinned=pinned, out=out, syn=syn, err=err,
+                       out_h=out_h, syn_h=syn_h, err_h=err_h)
+    torch.cuda.synchronize()
+
+    def step(ev_pair=None):
+        for n in SWEEP_CODES:
+            b = bufs[n]
+            if ev_pair is not None and n == ROOFLINE_N:
+                ev_pair[0].record(stream_h)
+            rc = hd.hd_decode(b["d_in"].data_ptr(), n * b["N"], n, b["N"], b["out"].data_ptr(), b["syn"].data_ptr(),
+                              hd.SYN_U8, b["err"].data_ptr(), sh)
+            if rc != 0:
+                raise hd.HDError(rc, "hd_decode")
+            if ev_pair is not None and n == ROOFLINE_N:
+                ev_pair[1].record(stream_h)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    kern_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    launches0 = hd.hd_launch_count()
+    with ClockSampler(uuid) as clk:
+        barrier()
+        t_start.record(stream_h)
+        for i in range(args.steps):
+            step(kern_events[i])
+        t_end.record(stream_h)
+        barrier()
+    launches = hd.hd_launch_count() - launches0
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    bits_per_step = sum(bufs[n]["N"] * bufs[n]["k"] for n in SWEEP_CODES)
+    value = bits_per_step * args.steps * world / (ms / 1e3) / 1e9
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kern_events]))
+    roof_bytes = algorithmic_bytes(ROOFLINE_N, SWEEP_N)
+    peak, peak_kind = peaks()
+    achieved = roof_bytes / (kern_ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    # end to end through the public API from pinned host buffers: H2D of each
+    # stream, decode, D2H of data bits, syndromes and err_count, every step
+    h2d = sum(bufs[n]["pinned"].numel() * 4 for n in SWEEP_CODES)
+    d2h = sum(bufs[n]["out"].numel() * 4 + bufs[n]["syn"].numel() + 8 for n in SWEEP_CODES)
+
+    def e2e_step():
+        for n in SWEEP_CODES:
+            b = bufs[n]
+            b["d_in"].copy_(b["pinned"], non_blocking=True)
+            hd.decode(b["d_in"], n, b["N"], syn_type=hd.SYN_U8, out=b["out"], syndromes=b["syn"],
+                      err_count=b["err"])
+            b["out_h"].copy_(b["out"], non_blocking=True)
+            b["syn_h"].copy_(b["syn"], non_blocking=True)
+            b["err_h"].copy_(b["err"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = bits_per_step * args.e2e_steps * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "num_codewords": SWEEP_N, "codes": list(SWEEP_CODES),
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (475 MB of streams and outputs, each touched once per step)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"hd_decode n={ROOFLINE_N}, N=2^24 ({roof_bytes} algorithmic bytes/launch, "
+                                   f"{kern_ms * 1e3:.2f} us avg)", "peak_kind": peak_kind},
+            "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,105 @@
+/*
+ * hd.h -- C ABI of the GB300 Hamming(n,k) decoder (libhd.so).
+ *
+ * The operation is the decoder of Islam, Kim and Kim, "Computationally
+ * Efficient Implementation of a Hamming Code Decoder using Graphics Processing
+ * Unit" (J. Commun. Netw., 2015): for each received codeword compute the
+ * checksum vector (Sec. III-C, Algorithm 1: checksum bit j is the modulo-2 sum
+ * of the bits at the positions of index set I_j, Sec. III-A), detect and
+ * correct the error it names, drop the checksum bits and merge the data bits
+ * into the decoded packet (Sec. II, Fig. 1; Sec. III, the "error" kernel).
+ *
+ * Codes: full-length Hamming codes n = 2^m - 1, 2 <= m <= 8 (n = 3..255),
+ * k = n - m data bits.  Positions are 1-indexed; the checksum bits sit at the
+ * power-of-two positions and use even parity; the data bits are the other
+ * positions in increasing order.
+ *
+ * Bit layout of every stream: bit b is bit (b mod 32) of uint32 word b/32
+ * (LSB first).  Codeword i occupies input bits [i*n, (i+1)*n) with position p
+ * at bit i*n + p - 1; its data bits go to output bits [i*k, (i+1)*k).
+ *
+ * Ownership and asynchrony: every buffer is caller-owned DEVICE memory unless
+ * a parameter says otherwise.  Calls enqueue work on `cuda_stream` (a
+ * cudaStream_t; NULL is the legacy default stream) and return before the work
+ * finishes.  The returned status covers argument checks and launch errors;
+ * a device-side failure (a bounded wait that ran out) is latched in a device
+ * status word that hd_device_status() reads.
+ *
+ * Alignment: stream, output and syndrome buffers must start on a 16-byte
+ * boundary (allocations from cudaMalloc or PyTorch always do).
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HD_OK = 0,
+    HD_ERR_INVALID_N = 1,   /* n is not 2^m - 1 with 2 <= m <= 8 */
+    HD_ERR_NULL = 2,        /* a required pointer is NULL */
+    HD_ERR_SIZE = 3,        /* in_bits != n * num_codewords, or a size is out of range */
+    HD_ERR_ALIGN = 4,       /* a buffer is not 16-byte aligned */
+    HD_ERR_CAPACITY = 5,    /* a fixed capacity would be exceeded */
+    HD_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+    HD_ERR_CUDA = 7,        /* the CUDA runtime reported an error */
+    HD_ERR_INVALID_ARG = 8  /* any other invalid argument */
+} hd_status;
+
+typedef enum {
+    HD_SYN_NONE = 0,  /* do not store syndromes */
+    HD_SYN_U8 = 1,    /* one uint8_t per codeword (valid for every supported n) */
+    HD_SYN_U16 = 2    /* one uint16_t per codeword */
+} hd_syn_type;
+
+/* Decode `num_codewords` back-to-back codewords of length n.
+ *
+ * stream        device, ceil(in_bits/32) words; pad bits past in_bits are ignored.
+ * in_bits       must equal n * num_codewords (HD_ERR_SIZE otherwise).
+ * out_bits      device, ceil(num_codewords*k/32) words; receives the data bits of
+ *               codeword i at bits [i*k, (i+1)*k); pad bits past num_codewords*k
+ *               in the last word are written as 0.
+ * syndromes     device, num_codewords elements of the width `syn_type` names, or
+ *               NULL with HD_SYN_NONE.  Element i is the checksum vector of codeword
+ *               i read as an integer (bit j = checksum bit j): 0 for a valid word,
+ *               otherwise the position that was flipped.
+ * err_count     device, one unsigned long long, or NULL: overwritten with the
+ *               number of codewords whose syndrome is nonzero.
+ * Two errors in one codeword give syndrome p XOR q and the decoder flips that
+ * third position, as any single-error-correcting Hamming decoder does.
+ * num_codewords == 0 is HD_OK; it only zeroes *err_count. */
+hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                    uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                    unsigned long long *err_count, void *cuda_stream);
+
+/* Encode `num_codewords` messages (the transmitter side of Sec. II: the
+ * checksum bits are added to the message).  data_bits holds message i at bits
+ * [i*k, (i+1)*k) (device, ceil(num_codewords*k/32) words); stream receives
+ * codeword i at bits [i*n, (i+1)*n) with even parity (device,
+ * ceil(num_codewords*n/32) words, pad bits written as 0). */
+hd_status hd_encode(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
+                    void *cuda_stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *hd_status_string(hd_status status);
+
+/* Reads and clears the device status word of the current device: 0 when no
+ * bounded device-side wait has run out since the last call, otherwise a
+ * nonzero code (HD_ERR_TIMEOUT).  Synchronises the device. */
+hd_status hd_device_status(uint32_t *status);
+
+/* Number of kernels this library has launched in this process (a host-side
+ * counter, incremented once per kernel launch it enqueues). */
+uint64_t hd_launch_count(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int hd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HD_H */

@@ -1,0 +1,121 @@
+// hd_api.cu -- the C ABI of libhd.so: argument checks and kernel dispatch for
+// the single-stream calls.  See include/hd.h for the contract.
+#include <cstdint>
+#include <mutex>
+
+#include "hd_internal.h"
+
+namespace hd {
+
+std::atomic<uint64_t> g_launches{0};
+
+int num_sms()
+{
+    static std::mutex mu;
+    static int cached[64];
+    static bool init = false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!init) {
+        for (int &c : cached) c = 0;
+        init = true;
+    }
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace hd
+
+using namespace hd;
+
+extern "C" {
+
+int hd_version(void) { return 100; }
+
+uint64_t hd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *hd_status_string(hd_status status)
+{
+    switch (status) {
+        case HD_OK: return "HD_OK";
+        case HD_ERR_INVALID_N: return "HD_ERR_INVALID_N: n must be 2^m-1 with 2<=m<=8";
+        case HD_ERR_NULL: return "HD_ERR_NULL: a required pointer is NULL";
+        case HD_ERR_SIZE: return "HD_ERR_SIZE: sizes do not match";
+        case HD_ERR_ALIGN: return "HD_ERR_ALIGN: buffer not 16-byte aligned";
+        case HD_ERR_CAPACITY: return "HD_ERR_CAPACITY: capacity exceeded";
+        case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT: a bounded device wait ran out";
+        case HD_ERR_CUDA: return "HD_ERR_CUDA: CUDA runtime error";
+        case HD_ERR_INVALID_ARG: return "HD_ERR_INVALID_ARG: invalid argument";
+    }
+    return "unknown hd_status";
+}
+
+hd_status hd_device_status(uint32_t *status)
+{
+    if (!status) return HD_ERR_NULL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HD_ERR_CUDA;
+    *status = read_clear_status_decode();
+    return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                    uint32_t *out_bits, void *syndromes, hd_syn_type syn_type, unsigned long long *err_count,
+                    void *cuda_stream)
+{
+    const int m = code_m(n);
+    if (m == 0) return HD_ERR_INVALID_N;
+    if (syn_type != HD_SYN_NONE && syn_type != HD_SYN_U8 && syn_type != HD_SYN_U16) return HD_ERR_INVALID_ARG;
+    if (num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+    if (in_bits != (uint64_t)n * num_codewords) return HD_ERR_SIZE;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (num_codewords == 0) {
+        if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
+        return HD_OK;
+    }
+    if (!stream || !out_bits) return HD_ERR_NULL;
+    if (syn_type != HD_SYN_NONE && !syndromes) return HD_ERR_NULL;
+    if (!aligned16(stream) || !aligned16(out_bits) || (syndromes && !aligned16(syndromes))) return HD_ERR_ALIGN;
+    const uint32_t k = n - (uint32_t)m;
+    const uint64_t in_words = words_for_bits(in_bits);
+    const uint64_t out_words = words_for_bits(num_codewords * k);
+    const int syn = syndromes ? (int)syn_type : 0;
+    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
+    uint64_t covered = 0;
+    if (launch_decode_fast(stream, n, num_codewords, out_bits, syndromes, syn, err_count, st, &covered) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    if (covered < num_codewords) {
+        const uint64_t tile_begin = covered / 32, tile_end = (num_codewords + 31) / 32;
+        if (launch_decode_generic(stream, in_words, n, num_codewords, tile_begin, tile_end, out_bits, out_words,
+                                  syndromes, syn, err_count, st) != cudaSuccess)
+            return HD_ERR_CUDA;
+    }
+    return HD_OK;
+}
+
+hd_status hd_encode(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
+                    void *cuda_stream)
+{
+    const int m = code_m(n);
+    if (m == 0) return HD_ERR_INVALID_N;
+    if (num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+    if (num_codewords == 0) return HD_OK;
+    if (!data_bits || !stream) return HD_ERR_NULL;
+    if (!aligned16(data_bits) || !aligned16(stream)) return HD_ERR_ALIGN;
+    const uint32_t k = n - (uint32_t)m;
+    if (launch_encode_generic(data_bits, words_for_bits(num_codewords * k), n, num_codewords, stream,
+                              words_for_bits(num_codewords * n), static_cast<cudaStream_t>(cuda_stream)) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// hd_internal.h -- host-side declarations shared by the translation units of
+// libhd.so.  Not installed; the public interface is include/hd.h.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hd.h"
+
+namespace hd {
+
+// Kernels launched by this library (hd_launch_count()).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t c = 1) { g_launches.fetch_add(c, std::memory_order_relaxed); }
+
+// m for n = 2^m - 1 (2 <= m <= 8), else 0.
+inline int code_m(uint32_t n)
+{
+    for (int m = 2; m <= 8; ++m)
+        if (n == (1u << m) - 1u) return m;
+    return 0;
+}
+
+inline uint64_t words_for_bits(uint64_t bits) { return (bits + 31) >> 5; }
+
+// Multiprocessor count of the current device (cached per device).
+int num_sms();
+
+// Generic warp-tile kernels (any supported n).  Warp tile t covers codewords
+// [32t, 32t+32); the launch covers warp tiles [tile_begin, tile_end).
+cudaError_t launch_decode_generic(const uint32_t *in, uint64_t in_words, uint32_t n, uint64_t num_cw,
+                                  uint64_t tile_begin, uint64_t tile_end, uint32_t *out, uint64_t out_words,
+                                  void *syn, int syn_type, unsigned long long *err, cudaStream_t st);
+cudaError_t launch_encode_generic(const uint32_t *data, uint64_t data_words, uint32_t n, uint64_t num_cw,
+                                  uint32_t *stream, uint64_t stream_words, cudaStream_t st);
+
+// Specialised streaming decoder.  Decodes the longest prefix of whole chunks
+// it supports and returns the number of codewords covered in *covered (0 when
+// n has no specialised kernel).
+cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
+                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered);
+
+// Device status words of the translation units whose kernels wait on barriers.
+uint32_t read_clear_status_decode();
+
+}  // namespace hd

@@ -1,0 +1,168 @@
+"""Thin Python binding of libhd.so.
+
+The ``hd_*`` functions mirror the C ABI of ``include/hd.h`` one to one (plain
+integers for pointers and the CUDA stream).  ``decode``/``encode`` add only
+argument marshalling for PyTorch tensors: device pointers, sizes and the
+current CUDA stream.  Every step of the decode runs in the library's kernels;
+there is no fallback of any kind, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libhd.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "hd.h")
+
+HD_OK = 0
+HD_ERR_INVALID_N = 1
+HD_ERR_NULL = 2
+HD_ERR_SIZE = 3
+HD_ERR_ALIGN = 4
+HD_ERR_CAPACITY = 5
+HD_ERR_TIMEOUT = 6
+HD_ERR_CUDA = 7
+HD_ERR_INVALID_ARG = 8
+
+SYN_NONE, SYN_U8, SYN_U16 = 0, 1, 2
+
+_lib = None
+
+_c = ctypes
+_vp, _u32, _u64, _i32 = _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int
+
+# name -> (restype, argtypes); every entry is declared in include/hd.h
+SIGNATURES = {
+    "hd_decode": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp]),
+    "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_status_string": (_c.c_char_p, [_i32]),
+    "hd_device_status": (_i32, [_c.POINTER(_u32)]),
+    "hd_launch_count": (_u64, []),
+    "hd_version": (_i32, []),
+}
+
+
+class HDError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1412_6862_gb300.build` "
+                               "(the decoder has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/hd.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hd_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().hd_status_string(int(status)).decode()
+    except RuntimeError:
+        return f"hd_status {status}"
+
+
+def check(status: int, what: str = "") -> None:
+    if status != HD_OK:
+        raise HDError(status, what)
+
+
+# ----------------------------------------------------------------------------
+# C-ABI mirrors
+# ----------------------------------------------------------------------------
+def hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, cuda_stream) -> int:
+    return lib().hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
+                           cuda_stream)
+
+
+def hd_encode(data_bits, n, num_codewords, stream, cuda_stream) -> int:
+    return lib().hd_encode(data_bits, n, num_codewords, stream, cuda_stream)
+
+
+def hd_device_status() -> int:
+    v = _u32(0)
+    check(lib().hd_device_status(ctypes.byref(v)), "hd_device_status")
+    return int(v.value)
+
+
+def hd_launch_count() -> int:
+    return int(lib().hd_launch_count())
+
+
+def hd_version() -> int:
+    return int(lib().hd_version())
+
+
+# ----------------------------------------------------------------------------
+# PyTorch marshalling
+# ----------------------------------------------------------------------------
+def code_params(n: int) -> tuple[int, int]:
+    """(m, k) for n = 2^m - 1, 2 <= m <= 8."""
+    for m in range(2, 9):
+        if n == (1 << m) - 1:
+            return m, n - m
+    raise HDError(HD_ERR_INVALID_N, f"n={n}")
+
+
+def words_for(bits: int) -> int:
+    return (int(bits) + 31) // 32
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def decode(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U8, out=None, syndromes=None,
+           err_count=None, cuda_stream=None):
+    """Decode a device tensor of packed stream words (int32/uint32, 16-byte aligned).
+
+    Returns (out_words int32 tensor, syndromes tensor or None, err_count int64
+    tensor of one element).  Outputs are allocated when not given."""
+    import torch
+    m, k = code_params(n)
+    dev = stream_words.device
+    if out is None:
+        out = torch.empty(max(1, words_for(num_codewords * k)), dtype=torch.int32, device=dev)
+    if syndromes is None and syn_type != SYN_NONE:
+        dt = torch.uint8 if syn_type == SYN_U8 else torch.int16
+        syndromes = torch.empty(max(1, num_codewords), dtype=dt, device=dev)
+    if err_count is None:
+        err_count = torch.empty(1, dtype=torch.int64, device=dev)
+    rc = hd_decode(_ptr(stream_words), n * num_codewords, n, num_codewords, _ptr(out),
+                   _ptr(syndromes) if syn_type != SYN_NONE else None, syn_type, _ptr(err_count),
+                   _stream_handle(cuda_stream))
+    check(rc, "hd_decode")
+    return out, syndromes, err_count
+
+
+def encode(data_words, n: int, num_codewords: int, out=None, cuda_stream=None):
+    """Encode a device tensor of packed message bits; returns the stream words."""
+    import torch
+    if out is None:
+        out = torch.empty(max(1, words_for(num_codewords * n)), dtype=torch.int32, device=data_words.device)
+    check(hd_encode(_ptr(data_words), n, num_codewords, _ptr(out), _stream_handle(cuda_stream)), "hd_encode")
+    return out

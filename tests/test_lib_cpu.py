@@ -1,0 +1,62 @@
+"""libhd.so builds for sm_103a, loads without a GPU, exports every function
+that include/hd.h declares, and rejects bad arguments on the host before any
+CUDA call."""
+import ctypes
+import shutil
+
+import pytest
+
+from paper_1412_6862_gb300 import build as hd_build
+from paper_1412_6862_gb300 import hd
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which(hd_build.nvcc()) is None and not hd_build.up_to_date():
+        pytest.skip("nvcc not available and libhd.so not built")
+    hd_build.build()
+    return hd.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(hd.LIB_PATH)
+    names = hd.header_functions()
+    assert "hd_decode" in names
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, f"declared in include/hd.h but not exported: {missing}"
+    # the binding describes every declared function and nothing else
+    assert sorted(hd.SIGNATURES) == names
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        assert hd.status_string(code).startswith("HD_")
+    assert hd.hd_version() >= 100
+
+
+def test_host_side_validation(lib):
+    # invalid n
+    assert hd.hd_decode(16, 8 * 4, 8, 4, 16, None, 0, None, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode(16, 511, 511, 1, 16, None, 0, None, None) == hd.HD_ERR_INVALID_N
+    # in_bits != n * num_codewords
+    assert hd.hd_decode(16, 7 * 4 + 1, 7, 4, 16, None, 0, None, None) == hd.HD_ERR_SIZE
+    # null pointers
+    assert hd.hd_decode(None, 7 * 4, 7, 4, 16, None, 0, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode(16, 7 * 4, 7, 4, None, None, 0, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode(16, 7 * 4, 7, 4, 16, None, hd.SYN_U8, None, None) == hd.HD_ERR_NULL
+    # alignment
+    assert hd.hd_decode(20, 7 * 4, 7, 4, 16, None, 0, None, None) == hd.HD_ERR_ALIGN
+    assert hd.hd_decode(16, 7 * 4, 7, 4, 24, None, 0, None, None) == hd.HD_ERR_ALIGN
+    # bad syndrome type
+    assert hd.hd_decode(16, 7 * 4, 7, 4, 16, None, 7, None, None) == hd.HD_ERR_INVALID_ARG
+    # zero codewords without err_count touches nothing
+    assert hd.hd_decode(None, 0, 7, 0, None, None, 0, None, None) == hd.HD_OK
+    assert hd.hd_encode(16, 9, 4, 16, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_encode(None, 7, 4, 16, None) == hd.HD_ERR_NULL
+    assert hd.hd_encode(20, 7, 4, 16, None) == hd.HD_ERR_ALIGN
+
+
+def test_no_launches_counted_for_rejected_calls(lib):
+    before = hd.hd_launch_count()
+    hd.hd_decode(16, 7 * 4 + 1, 7, 4, 16, None, 0, None, None)
+    assert hd.hd_launch_count() == before
