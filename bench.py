@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--codes", type=str, default=",".join(map(str, SWEEP_CODES)),
+                    help="subset of the sweep codes to run (profiling a single kernel)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -183,11 +186,16 @@ def cpu_baseline(seconds):
     per_code = calibrate_oracle(threads, seconds)
     streams = oracle_sample_inputs(SWEEP_CODES, per_code)
     t0 = time.perf_counter()
-    bits = oracle_decode_all(streams, per_code, threads)
+    bits, passes = 0, 0
+    while True:
+        bits += oracle_decode_all(streams, per_code, threads)
+        passes += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
     dt = time.perf_counter() - t0
     return {"value": bits / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {per_code[15]}/{per_code[31]}/{per_code[63]} codewords of the (15,11)/(31,26)/(63,57) "
-                      f"streams, bit-by-bit C oracle on {threads} host threads, {dt:.1f} s"}
+            "sample": f"{passes} pass(es) over the first {per_code[15]}/{per_code[31]}/{per_code[63]} codewords of the "
+                      f"(15,11)/(31,26)/(63,57) streams, bit-by-bit C oracle on {threads} host threads, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -233,10 +241,13 @@ def run_ours(args):
     hd_build.build()
     from paper_1412_6862_gb300 import hd, synth
 
+    codes = tuple(int(c) for c in args.codes.split(","))
+    assert all(c in SWEEP_CODES for c in codes), codes
+    roof_n = ROOFLINE_N if ROOFLINE_N in codes else max(codes)
     stream_h = torch.cuda.current_stream(dev)
     sh = int(stream_h.cuda_stream)
     bufs = {}
-    for n in SWEEP_CODES:
+    for n in codes:
         m, k = code_params(n)
         N = SWEEP_N
         seed = n + 1000 * rank
@@ -258,17 +269,12 @@ def run_ours(args):
                        out_h=out_h, syn_h=syn_h, err_h=err_h)
     torch.cuda.synchronize()
 
-    def step(ev_pair=None):
-        for n in SWEEP_CODES:
-            b = bufs[n]
-            if ev_pair is not None and n == ROOFLINE_N:
-                ev_pair[0].record(stream_h)
-            rc = hd.hd_decode(b["d_in"].data_ptr(), n * b["N"], n, b["N"], b["out"].data_ptr(), b["syn"].data_ptr(),
-                              hd.SYN_U8, b["err"].data_ptr(), sh)
-            if rc != 0:
-                raise hd.HDError(rc, "hd_decode")
-            if ev_pair is not None and n == ROOFLINE_N:
-                ev_pair[1].record(stream_h)
+    def decode_call(n, cuda_stream):
+        b = bufs[n]
+        rc = hd.hd_decode(b["d_in"].data_ptr(), n * b["N"], n, b["N"], b["out"].data_ptr(), b["syn"].data_ptr(),
+                          hd.SYN_U8, b["err"].data_ptr(), cuda_stream)
+        if rc != 0:
+            raise hd.HDError(rc, "hd_decode")
 
     def barrier():
         if world > 1:
@@ -276,7 +282,27 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        for n in codes:
+            decode_call(n, sh)
+    barrier()
+
+    # One step = graph A (the roofline kernel's decode) + graph B (the other
+    # codes), replayed from CUDA graphs; events between the replays time
+    # graph A on the stream it runs on.
+    others = [n for n in codes if n != roof_n]
+    graph_a, graph_b = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    l0 = hd.hd_launch_count()
+    with torch.cuda.graph(graph_a):
+        decode_call(roof_n, torch.cuda.current_stream().cuda_stream)
+    if others:
+        with torch.cuda.graph(graph_b):
+            for n in others:
+                decode_call(n, torch.cuda.current_stream().cuda_stream)
+    launches_per_step = hd.hd_launch_count() - l0
+    for _ in range(3):
+        graph_a.replay()
+        if others:
+            graph_b.replay()
     barrier()
 
     uuid = None
@@ -288,35 +314,38 @@ def run_ours(args):
                    for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    launches0 = hd.hd_launch_count()
     with ClockSampler(uuid) as clk:
         barrier()
         t_start.record(stream_h)
         for i in range(args.steps):
-            step(kern_events[i])
+            kern_events[i][0].record(stream_h)
+            graph_a.replay()
+            kern_events[i][1].record(stream_h)
+            if others:
+                graph_b.replay()
         t_end.record(stream_h)
         barrier()
-    launches = hd.hd_launch_count() - launches0
+    launches = launches_per_step * args.steps
     ms = t_start.elapsed_time(t_end)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    bits_per_step = sum(bufs[n]["N"] * bufs[n]["k"] for n in SWEEP_CODES)
+    bits_per_step = sum(bufs[n]["N"] * bufs[n]["k"] for n in codes)
     value = bits_per_step * args.steps * world / (ms / 1e3) / 1e9
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kern_events]))
-    roof_bytes = algorithmic_bytes(ROOFLINE_N, SWEEP_N)
+    roof_bytes = algorithmic_bytes(roof_n, SWEEP_N)
     peak, peak_kind = peaks()
     achieved = roof_bytes / (kern_ms / 1e3) / 1e9
     clocks = clk.summary()
 
     # end to end through the public API from pinned host buffers: H2D of each
     # stream, decode, D2H of data bits, syndromes and err_count, every step
-    h2d = sum(bufs[n]["pinned"].numel() * 4 for n in SWEEP_CODES)
-    d2h = sum(bufs[n]["out"].numel() * 4 + bufs[n]["syn"].numel() + 8 for n in SWEEP_CODES)
+    h2d = sum(bufs[n]["pinned"].numel() * 4 for n in codes)
+    d2h = sum(bufs[n]["out"].numel() * 4 + bufs[n]["syn"].numel() + 8 for n in codes)
 
     def e2e_step():
-        for n in SWEEP_CODES:
+        for n in codes:
             b = bufs[n]
             b["d_in"].copy_(b["pinned"], non_blocking=True)
             hd.decode(b["d_in"], n, b["N"], syn_type=hd.SYN_U8, out=b["out"], syndromes=b["syn"],
@@ -326,19 +355,20 @@ def run_ours(args):
             b["err_h"].copy_(b["err"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
-    for _ in range(3):
+    e2e_steps = 0 if args.no_e2e else args.e2e_steps
+    for _ in range(3 if e2e_steps else 0):
         e2e_step()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = bits_per_step * args.e2e_steps * world / e2e_s / 1e9
+    e2e_value = bits_per_step * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -349,12 +379,13 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "num_codewords": SWEEP_N, "codes": list(SWEEP_CODES),
+            "config": {"workload": WORKLOAD if codes == SWEEP_CODES else f"subset {codes} of: {WORKLOAD}",
+                       "num_codewords": SWEEP_N, "codes": list(codes),
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (475 MB of streams and outputs, each touched once per step)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": f"hd_decode n={ROOFLINE_N}, N=2^24 ({roof_bytes} algorithmic bytes/launch, "
+                         "kernel": f"hd_decode n={roof_n}, N=2^24 ({roof_bytes} algorithmic bytes/launch, "
                                    f"{kern_ms * 1e3:.2f} us avg)", "peak_kind": peak_kind},
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

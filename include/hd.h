@@ -83,6 +83,51 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
 hd_status hd_encode(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
                     void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Kernel configurations and the autotuner.
+ *
+ * Long streams are decoded by a streaming kernel compiled in several
+ * configurations per (n, syn_type): codewords per thread, threads per CTA,
+ * pipeline depth and whether decoded words overwrite the input stage.  A
+ * built-in choice measured on GB300 is used until hd_autotune() times every
+ * configuration on the current device and keeps the fastest, or
+ * hd_variant_select() pins one.  Choices are per device and per process.
+ * The configuration never changes the result, only the speed.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t index;                /* ordinal among the configurations of (n, syn_type) */
+    uint32_t n;
+    uint32_t syn_type;
+    uint32_t codewords_per_thread; /* 8, 16 or 32 */
+    uint32_t threads;              /* threads per CTA */
+    uint32_t stages;               /* input pipeline depth (shared-memory stages) */
+    uint32_t inplace;              /* 1: decoded words overwrite their input stage */
+    uint32_t smem_bytes;           /* dynamic shared memory per CTA */
+    uint64_t chunk_codewords;      /* codewords per CTA iteration */
+    int32_t blocks_per_sm;         /* resident CTAs per SM on the current device */
+    float measured_us;             /* autotuner time of the request, -1 when not measured */
+} hd_variant_info;
+
+/* Number of compiled configurations for (n, syn_type).  Host only. */
+hd_status hd_variant_count(uint32_t n, hd_syn_type syn_type, uint32_t *count);
+
+/* Describe configuration `ordinal` (0 .. count-1) of (n, syn_type). */
+hd_status hd_variant_info_get(uint32_t n, hd_syn_type syn_type, uint32_t ordinal, hd_variant_info *info);
+
+/* Pin configuration `ordinal` for (n, syn_type) on the current device;
+ * ordinal < 0 restores the built-in choice. */
+hd_status hd_variant_select(uint32_t n, hd_syn_type syn_type, int32_t ordinal);
+
+/* The configuration hd_decode() uses now for (n, syn_type). */
+hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *info);
+
+/* Time every configuration of (n, syn_type) on `num_codewords` codewords of
+ * scratch data (allocated and freed here; `reps` timed launches each, 0 = 5)
+ * on `cuda_stream`, keep the fastest for this device and report it in
+ * *chosen (may be NULL).  Synchronises the stream. */
+hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,
+                      hd_variant_info *chosen);
+
 /* Human-readable name of a status code (static storage). */
 const char *hd_status_string(hd_status status);
 

@@ -1,184 +1,317 @@
-// hd_decode.cu -- streaming decoder for long single-n streams on sm_103a.
-//
-// Persistent CTAs walk the stream in chunks of T thread tiles (32*T
-// codewords, T*n input words, T*k output words).  One elected thread streams
-// the input chunks into an S-stage shared-memory ring with 1-D bulk copies
-// (cp.async.bulk, completing on an mbarrier per stage); every thread decodes
-// its own 32-codeword tile out of shared memory (stride n words between
-// threads, conflict-free because n is odd); the decoded words and syndromes
-// go to a double-buffered shared staging area that the elected thread writes
-// back with bulk stores.  HBM sees exactly one read of every input byte and
-// one write of every output byte.
-#include <cstdint>
+// hd_decode.cu -- registry of the compiled streaming-decoder configurations,
+// per-device launch setup, the configuration choice (built-in defaults or the
+// autotuner's measured pick) and the device status word.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
-#include "hd_device.cuh"
 #include "hd_internal.h"
-#include "hd_tile.cuh"
+#include "hd_stream.cuh"
 
 namespace hd {
+
+void register_stream_a(std::vector<StreamVariant> &v);
+void register_stream_b(std::vector<StreamVariant> &v);
+void register_stream_c(std::vector<StreamVariant> &v);
+
 namespace {
 
-__device__ uint32_t g_status_decode;
+__device__ uint32_t g_hd_status;
 
-template <int N_, int SYN, int T, int S>
-struct StreamCfg {
-    using C = Code<N_>;
-    static constexpr int SB = SYN == 2 ? 2 : 1;
-    static constexpr uint32_t in_bytes = T * N_ * 4;
-    static constexpr uint32_t out_bytes = T * C::k * 4;
-    static constexpr uint32_t syn_bytes = SYN ? T * 32 * SB : 0;
-    static constexpr uint32_t off_in = 128;
-    static constexpr uint32_t off_out = off_in + S * in_bytes;
-    static constexpr uint32_t off_syn = off_out + 2 * out_bytes;
-    static constexpr uint32_t smem = off_syn + 2 * syn_bytes;
-    static constexpr int V = (C::k % 4 == 0) ? 4 : (C::k % 2 == 0) ? 2 : 1;
-    static_assert(in_bytes % 16 == 0 && out_bytes % 16 == 0 && syn_bytes % 16 == 0, "bulk copies need 16B sizes");
+std::mutex g_mu;
+
+const std::vector<StreamVariant> &variants()
+{
+    static const std::vector<StreamVariant> v = [] {
+        std::vector<StreamVariant> a;
+        register_stream_a(a);
+        register_stream_b(a);
+        register_stream_c(a);
+        return a;
+    }();
+    return v;
+}
+
+int current_device()
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+// (device, kernel) -> resident CTAs per SM (0 = not yet configured)
+std::map<std::pair<int, const void *>, int> g_bps;
+// (device, n, syn) -> chosen variant index (autotuner or explicit selection)
+std::map<std::tuple<int, uint32_t, int>, int> g_choice;
+// device -> address of g_hd_status
+std::map<int, uint32_t *> g_status_ptr;
+
+// Built-in choice per (n, G, T, S, inplace), measured on GB300; used until the
+// autotuner or the caller picks another configuration.
+struct DefaultCfg {
+    uint32_t n;
+    int G, T, S, inplace;
+};
+constexpr DefaultCfg kDefaults[] = {
+    {7, 32, 128, 4, 1},  {15, 32, 512, 2, 1}, {31, 32, 128, 4, 1},
+    {63, 32, 128, 2, 1}, {127, 8, 256, 3, 1}, {255, 8, 128, 2, 1},
 };
 
-template <int N_, int SYN, int T, int S>
-__global__ void __launch_bounds__(T)
-    k_decode_stream(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint8_t *__restrict__ syn,
-                    unsigned long long *__restrict__ err, uint64_t nchunks)
+int find_variant(uint32_t n, int syn, int G, int T, int S, int inplace)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S>;
-    constexpr int K = Code<N_>::k;
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_in = reinterpret_cast<uint32_t *>(smem + Cfg::off_in);
-    uint32_t *s_out = reinterpret_cast<uint32_t *>(smem + Cfg::off_out);
-    uint8_t *s_syn = smem + Cfg::off_syn;
-    const int tid = threadIdx.x;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const uint64_t c = blockIdx.x + (uint64_t)s * gridDim.x;
-            if (c < nchunks) {
-                mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
-                bulk_g2s(s_in + s * T * N_, in + c * (uint64_t)(T * N_), Cfg::in_bytes, &bar[s]);
-            }
-        }
-    }
-
-    uint32_t errs = 0;
-    uint32_t it = 0;
-    bool aborted = false;
-    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x, ++it) {
-        const int s = (int)(it % S);
-        const uint32_t parity = (it / S) & 1u;
-        const int ob = (int)(it & 1u);
-        const bool ok = mbar_wait_bounded(&bar[s], parity);
-        if (tid == 0) bulk_wait_read<1>();  // staging buffer ob is no longer read by the store of it-2
-        if (__syncthreads_or(!ok)) {
-            aborted = true;
-            break;
-        }
-        {
-            uint32_t r[N_];
-            const uint32_t *src = s_in + s * T * N_ + tid * N_;
-#pragma unroll
-            for (int w = 0; w < N_; ++w) r[w] = src[w];
-            OutPacker<Cfg::V> op(s_out + ob * T * K + tid * K);
-            SynPacker<Cfg::SB, SYN != 0> sp(s_syn + ob * Cfg::syn_bytes + tid * 32 * Cfg::SB);
-            decode_thread_tile<N_>(r, op, sp);
-            errs += sp.nonzero();
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            bulk_s2g(out + c * (uint64_t)(T * K), s_out + ob * T * K, Cfg::out_bytes);
-            if constexpr (SYN != 0)
-                bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
-            bulk_commit();
-            const uint64_t cn = c + (uint64_t)S * gridDim.x;
-            if (cn < nchunks) {
-                mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
-                bulk_g2s(s_in + s * T * N_, in + cn * (uint64_t)(T * N_), Cfg::in_bytes, &bar[s]);
-            }
-        }
-    }
-    if (aborted && tid == 0) {
-        atomicOr(&g_status_decode, (uint32_t)HD_ERR_TIMEOUT);
-        // Wait (bounded) for every load still in flight into this CTA's ring.
-        for (uint32_t j = it; j < it + S; ++j) {
-            const uint64_t cj = blockIdx.x + (uint64_t)j * gridDim.x;
-            if (cj < nchunks) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
-        }
-    }
-    if (tid == 0) bulk_wait_all<0>();
-    if (err != nullptr) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
-        if ((tid & 31) == 0 && errs != 0) atomicAdd(err, (unsigned long long)errs);
-    }
+    const auto &v = variants();
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].n == n && v[i].syn == syn && v[i].G == G && v[i].T == T && v[i].S == S && v[i].inplace == inplace)
+            return (int)i;
+    return -1;
 }
 
-template <int N_, int SYN, int T, int S>
-cudaError_t launch_stream(const uint32_t *in, uint64_t num_cw, uint32_t *out, void *syn, unsigned long long *err,
-                          cudaStream_t st, uint64_t *covered)
+int default_variant(uint32_t n, int syn)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S>;
-    const uint64_t nchunks = num_cw / (32ull * T);
-    *covered = nchunks * 32ull * T;
-    if (nchunks == 0) return cudaSuccess;
-    auto kern = k_decode_stream<N_, SYN, T, S>;
-    static int configured_dev = -1;
-    static int blocks_per_sm = 1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, T, Cfg::smem);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-        configured_dev = dev;
-    }
-    const uint64_t cap = (uint64_t)num_sms() * blocks_per_sm;
-    const int grid = (int)(nchunks < cap ? nchunks : cap);
-    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, nchunks);
-    count_launch();
-    return cudaGetLastError();
+    for (const auto &d : kDefaults)
+        if (d.n == n) {
+            const int i = find_variant(n, syn, d.G, d.T, d.S, d.inplace);
+            if (i >= 0) return i;
+        }
+    const auto &v = variants();
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].n == n && v[i].syn == syn) return (int)i;
+    return -1;
 }
 
-template <int N_, int T, int S>
-cudaError_t launch_stream_syn(const uint32_t *in, uint64_t num_cw, uint32_t *out, void *syn, int syn_type,
-                              unsigned long long *err, cudaStream_t st, uint64_t *covered)
+int chosen_variant(uint32_t n, int syn)
 {
-    switch (syn_type) {
-        case 1: return launch_stream<N_, 1, T, S>(in, num_cw, out, syn, err, st, covered);
-        case 2: return launch_stream<N_, 2, T, S>(in, num_cw, out, syn, err, st, covered);
-        default: return launch_stream<N_, 0, T, S>(in, num_cw, out, syn, err, st, covered);
-    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_choice.find({current_device(), n, syn});
+    if (it != g_choice.end()) return it->second;
+    return default_variant(n, syn);
 }
 
 }  // namespace
 
-cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
-                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered)
+int stream_blocks_per_sm(const void *kernel, int threads, uint32_t smem)
 {
-    *covered = 0;
-    switch (n) {
-        case 7: return launch_stream_syn<7, 256, 4>(in, num_cw, out, syn, syn_type, err, st, covered);
-        case 15: return launch_stream_syn<15, 256, 4>(in, num_cw, out, syn, syn_type, err, st, covered);
-        case 31: return launch_stream_syn<31, 128, 4>(in, num_cw, out, syn, syn_type, err, st, covered);
-        case 63: return launch_stream_syn<63, 64, 4>(in, num_cw, out, syn, syn_type, err, st, covered);
-        default: return cudaSuccess;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    int &b = g_bps[{dev, kernel}];
+    if (b == 0) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess) return -1;
+        b = v > 0 ? v : -1;
     }
+    return b;
+}
+
+uint32_t *status_ptr()
+{
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    uint32_t *&p = g_status_ptr[dev];
+    if (p == nullptr) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_hd_status) != cudaSuccess) return nullptr;
+        p = static_cast<uint32_t *>(a);
+    }
+    return p;
 }
 
 uint32_t read_clear_status_decode()
 {
     uint32_t v = 0, zero = 0;
-    cudaMemcpyFromSymbol(&v, g_status_decode, sizeof(v));
-    cudaMemcpyToSymbol(g_status_decode, &zero, sizeof(zero));
+    cudaMemcpyFromSymbol(&v, g_hd_status, sizeof(v));
+    cudaMemcpyToSymbol(g_hd_status, &zero, sizeof(zero));
     return v;
 }
 
+cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
+                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered)
+{
+    *covered = 0;
+    const int idx = chosen_variant(n, syn_type);
+    if (idx < 0) return cudaSuccess;
+    const StreamVariant &v = variants()[idx];
+    const uint64_t nchunks = num_cw / v.chunk_cw;
+    if (nchunks == 0) return cudaSuccess;
+    uint32_t *status = status_ptr();
+    if (status == nullptr) return cudaErrorInvalidSymbol;
+    *covered = nchunks * v.chunk_cw;
+    return v.launch(v, in, nchunks, out, syn, err, status, st);
+}
+
+// ---------------------------------------------------------------------------
+// Variant queries, explicit selection and the autotuner (C ABI in hd.h)
+// ---------------------------------------------------------------------------
+static void fill_info(int idx, hd_variant_info *info)
+{
+    const StreamVariant &v = variants()[idx];
+    std::memset(info, 0, sizeof(*info));
+    info->index = (uint32_t)idx;
+    info->n = v.n;
+    info->syn_type = (uint32_t)v.syn;
+    info->codewords_per_thread = (uint32_t)v.G;
+    info->threads = (uint32_t)v.T;
+    info->stages = (uint32_t)v.S;
+    info->inplace = (uint32_t)v.inplace;
+    info->smem_bytes = v.smem;
+    info->chunk_codewords = v.chunk_cw;
+    info->blocks_per_sm = stream_blocks_per_sm(v.kernel, v.T, v.smem);
+    info->measured_us = -1.0f;
+}
+
 }  // namespace hd
+
+using namespace hd;
+
+extern "C" {
+
+hd_status hd_variant_count(uint32_t n, hd_syn_type syn_type, uint32_t *count)
+{
+    if (!count) return HD_ERR_NULL;
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    uint32_t c = 0;
+    for (const auto &v : variants())
+        if (v.n == n && v.syn == (int)syn_type) ++c;
+    *count = c;
+    return HD_OK;
+}
+
+hd_status hd_variant_info_get(uint32_t n, hd_syn_type syn_type, uint32_t ordinal, hd_variant_info *info)
+{
+    if (!info) return HD_ERR_NULL;
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    uint32_t c = 0;
+    const auto &v = variants();
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (v[i].n == n && v[i].syn == (int)syn_type) {
+            if (c == ordinal) {
+                fill_info((int)i, info);
+                info->index = ordinal;
+                return HD_OK;
+            }
+            ++c;
+        }
+    }
+    return HD_ERR_INVALID_ARG;
+}
+
+hd_status hd_variant_select(uint32_t n, hd_syn_type syn_type, int32_t ordinal)
+{
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ordinal < 0) {
+        g_choice.erase({dev, n, (int)syn_type});
+        return HD_OK;
+    }
+    int32_t c = 0;
+    const auto &v = variants();
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (v[i].n == n && v[i].syn == (int)syn_type) {
+            if (c == ordinal) {
+                g_choice[{dev, n, (int)syn_type}] = (int)i;
+                return HD_OK;
+            }
+            ++c;
+        }
+    }
+    return HD_ERR_INVALID_ARG;
+}
+
+hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *info)
+{
+    if (!info) return HD_ERR_NULL;
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    const int idx = chosen_variant(n, (int)syn_type);
+    if (idx < 0) return HD_ERR_INVALID_ARG;
+    fill_info(idx, info);
+    // report the ordinal within (n, syn) rather than the global index
+    uint32_t c = 0;
+    const auto &v = variants();
+    for (int i = 0; i < idx; ++i)
+        if (v[i].n == n && v[i].syn == (int)syn_type) ++c;
+    info->index = c;
+    return HD_OK;
+}
+
+hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,
+                      hd_variant_info *chosen)
+{
+    const int m = code_m(n);
+    if (m == 0) return HD_ERR_INVALID_N;
+    if (syn_type != HD_SYN_NONE && syn_type != HD_SYN_U8 && syn_type != HD_SYN_U16) return HD_ERR_INVALID_ARG;
+    if (num_codewords == 0 || num_codewords > (1ull << 32)) return HD_ERR_SIZE;
+    if (reps == 0) reps = 5;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const uint32_t k = n - (uint32_t)m;
+    const size_t in_b = words_for_bits(num_codewords * n) * 4 + 16;
+    const size_t out_b = words_for_bits(num_codewords * k) * 4 + 16;
+    const size_t syn_b = num_codewords * 2 + 16;
+    void *din = nullptr, *dout = nullptr, *dsyn = nullptr, *derr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hd_status rc = HD_OK;
+    int best = -1;
+    float best_us = 0.f;
+    if (cudaMalloc(&din, in_b) != cudaSuccess || cudaMalloc(&dout, out_b) != cudaSuccess ||
+        cudaMalloc(&dsyn, syn_b) != cudaSuccess || cudaMalloc(&derr, 8) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = HD_ERR_CUDA;
+    }
+    uint32_t *status = status_ptr();
+    if (rc == HD_OK && status == nullptr) rc = HD_ERR_CUDA;
+    if (rc == HD_OK && cudaMemsetAsync(din, 0x5A, in_b, st) != cudaSuccess) rc = HD_ERR_CUDA;
+    const auto &vs = variants();
+    for (size_t i = 0; rc == HD_OK && i < vs.size(); ++i) {
+        const StreamVariant &v = vs[i];
+        if (v.n != n || v.syn != (int)syn_type) continue;
+        const uint64_t nchunks = num_codewords / v.chunk_cw;
+        if (nchunks == 0) continue;
+        if (stream_blocks_per_sm(v.kernel, v.T, v.smem) <= 0) continue;
+        void *sy = syn_type == HD_SYN_NONE ? nullptr : dsyn;
+        auto *er = static_cast<unsigned long long *>(derr);
+        if (v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status,
+                     st) != cudaSuccess) {
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        cudaEventRecord(e0, st);
+        for (uint32_t r = 0; r < reps; ++r)
+            v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        // normalise to the whole request (the chunked prefix differs per variant)
+        const float us = ms * 1000.f / (float)reps * (float)num_codewords / (float)(nchunks * v.chunk_cw);
+        if (best < 0 || us < best_us) {
+            best = (int)i;
+            best_us = us;
+        }
+    }
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    if (dsyn) cudaFree(dsyn);
+    if (derr) cudaFree(derr);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != HD_OK) return rc;
+    if (best < 0) return HD_ERR_SIZE;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_choice[{current_device(), n, (int)syn_type}] = best;
+    }
+    if (chosen) {
+        hd_variant_current(n, syn_type, chosen);
+        chosen->measured_us = best_us;
+    }
+    return HD_OK;
+}
+
+}  // extern "C"

@@ -41,7 +41,9 @@ cudaError_t launch_encode_generic(const uint32_t *data, uint64_t data_words, uin
 cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
                                int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered);
 
-// Device status words of the translation units whose kernels wait on barriers.
+// Device address of the status word that kernels latch HD_ERR_TIMEOUT into
+// (per device; nullptr on failure), and its host-side read-and-clear.
+uint32_t *status_ptr();
 uint32_t read_clear_status_decode();
 
 }  // namespace hd

@@ -1,0 +1,265 @@
+// hd_stream.cuh -- the streaming decoder kernel for long single-n streams.
+//
+// Persistent CTAs whose warps each walk the stream in chunks of 32*G codewords
+// (G per thread, so G tiles of 32 codewords per warp).  Lane 0 of every warp
+// streams the warp's input chunks into its own S-stage shared-memory ring with
+// 1-D bulk copies (cp.async.bulk completing on one mbarrier per stage); every
+// thread decodes its part out of shared memory; the decoded words and
+// syndromes are staged in shared memory and written back with bulk stores.
+// HBM sees one read of every input byte and one write of every output byte.
+//
+// INPLACE: the decoded words overwrite the chunk's own input stage (the warp
+// first copies the chunk to registers), which removes the output staging
+// buffers so that more warps fit on an SM; the stage is refilled once its bulk
+// store has finished reading it.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "hd_device.cuh"
+#include "hd_internal.h"
+#include "hd_tile.cuh"
+
+namespace hd {
+
+// One compiled configuration of the streaming decoder.
+struct StreamVariant {
+    uint32_t n;
+    int syn;      // 0 none, 1 u8, 2 u16
+    int G;        // codewords per thread
+    int T;        // threads per CTA
+    int S;        // input stages per warp
+    int inplace;  // output written into the input stage
+    uint32_t smem;
+    uint64_t chunk_cw;  // codewords per warp iteration (32*G)
+    cudaError_t (*launch)(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out, void *syn,
+                          unsigned long long *err, uint32_t *status, cudaStream_t st);
+    const void *kernel;
+};
+
+// Every warp is an independent pipeline: it owns S input stages with one
+// mbarrier each, (unless INPLACE) two output staging buffers, and two syndrome
+// buffers.  Lane 0 issues the warp's bulk loads and stores; warps never wait
+// for one another, so one warp's memory wait overlaps the others' arithmetic.
+template <int N_, int SYN, int T, int S, int G, int INPLACE>
+struct StreamCfg {
+    using C = Code<N_>;
+    static constexpr int WARPS = T / 32;
+    static constexpr int H = 32 / G;                       // threads per 32-codeword tile
+    static constexpr int TEAMS = 32 / H;                   // tiles per warp chunk
+    static constexpr int SB = SYN == 2 ? 2 : 1;            // syndrome bytes (packing width)
+    static constexpr bool WIDE = (SB == 1 && C::m == 8);   // u8 lanes may use bit 7
+    static constexpr int GK = G * C::k;                    // output bits per thread
+    static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
+    static constexpr int R = (G * N_ + 31) / 32;           // input words per thread after re-alignment
+    static constexpr uint32_t in_words = TEAMS * N_;       // per warp chunk
+    static constexpr uint32_t in_bytes = in_words * 4;
+    static constexpr uint32_t stage_bytes = in_bytes + 16;  // one spare 16-byte group for the funnel read
+    static constexpr uint32_t out_words = TEAMS * C::k;
+    static constexpr uint32_t out_bytes = out_words * 4;
+    static constexpr uint32_t out_buf_bytes = (out_bytes + 15) / 16 * 16 + 16;  // room for the last spill word
+    static constexpr uint32_t syn_bytes = SYN ? 32 * G * SB : 0;
+    // per-warp layout
+    static constexpr uint32_t off_bar = 0;
+    static constexpr uint32_t off_in = 64;
+    static constexpr uint32_t off_out = off_in + S * stage_bytes;
+    static constexpr uint32_t off_syn = off_out + (INPLACE ? 0 : 2 * out_buf_bytes);
+    static constexpr uint32_t warp_bytes = (off_syn + 2 * syn_bytes + 127) / 128 * 128;
+    static constexpr uint32_t smem = WARPS * warp_bytes;
+    static constexpr int V = !ALIGNED                                ? 1
+                             : (C::k % 4 == 0 && (GK / 32) % 4 == 0) ? 4
+                             : (C::k % 2 == 0 && (GK / 32) % 2 == 0) ? 2
+                                                                     : 1;
+    static_assert(T % 32 == 0 && S <= 8, "whole warps, at most 8 stages");
+    static_assert(in_bytes % 16 == 0 && out_bytes % 16 == 0 && syn_bytes % 16 == 0, "bulk copies need 16B sizes");
+    static_assert(stage_bytes % 16 == 0 && out_buf_bytes % 16 == 0, "16B-aligned buffers");
+    static_assert(smem <= 232448, "shared memory per CTA");
+    static_assert(!INPLACE || out_bytes + 16 <= stage_bytes, "in-place output fits the input stage");
+    static_assert(!INPLACE || S >= 2, "in-place refills lag one iteration");
+};
+
+template <int N_, int SYN, int T, int S, int G, int INPLACE>
+__global__ void __launch_bounds__(T)
+    k_decode_stream(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint8_t *__restrict__ syn,
+                    unsigned long long *__restrict__ err, uint32_t *__restrict__ status, uint64_t nchunks)
+{
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
+    using C = Code<N_>;
+    constexpr int K = C::k;
+    constexpr int H = Cfg::H;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *wbase = smem + warp * Cfg::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
+    uint8_t *s_in = wbase + Cfg::off_in;
+    uint8_t *s_out = wbase + Cfg::off_out;
+    uint8_t *s_syn = wbase + Cfg::off_syn;
+    const int team = lane / H, h = lane % H;
+    // this thread's part inside its tile
+    const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * N_);
+    const uint32_t in_w = team * N_ + (in_bit >> 5), in_sh = in_bit & 31u;
+    const uint32_t out_bit = (uint32_t)h * (uint32_t)Cfg::GK;
+    const uint32_t out_w = team * K + (out_bit >> 5), out_sh = out_bit & 31u;
+    const uint32_t syn_off = (uint32_t)lane * G * Cfg::SB;
+    const uint64_t gw = (uint64_t)blockIdx.x * Cfg::WARPS + warp;  // global warp index
+    const uint64_t tw = (uint64_t)gridDim.x * Cfg::WARPS;          // warps in the grid
+
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const uint64_t c = gw + (uint64_t)s * tw;
+            if (c < nchunks) {
+                mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
+                bulk_g2s(s_in + s * Cfg::stage_bytes, in + c * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
+            }
+        }
+    }
+    __syncwarp();
+
+    uint32_t errs = 0;
+    uint32_t it = 0;
+    bool aborted = false;
+    for (uint64_t c = gw; c < nchunks; c += tw, ++it) {
+        const int s = (int)(it % S);
+        const uint32_t parity = (it / S) & 1u;
+        const int ob = (int)(it & 1u);
+        const bool ok = mbar_wait_bounded(&bar[s], parity);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            aborted = true;
+            break;
+        }
+        const uint32_t *stage = reinterpret_cast<const uint32_t *>(s_in + s * Cfg::stage_bytes);
+        uint32_t r[Cfg::R];
+        if constexpr (H == 1) {
+#pragma unroll
+            for (int w = 0; w < Cfg::R; ++w) r[w] = stage[in_w + w];
+        } else {
+            uint32_t lo = stage[in_w];
+#pragma unroll
+            for (int w = 0; w < Cfg::R; ++w) {
+                const uint32_t hi = stage[in_w + w + 1];
+                r[w] = __funnelshift_r(lo, hi, in_sh);
+                lo = hi;
+            }
+        }
+        __syncwarp();  // the whole chunk is in registers
+        if (lane == 0) {
+            if constexpr (!INPLACE) {
+                // the stage is free again: prefetch the chunk S iterations ahead into it
+                const uint64_t cn = c + (uint64_t)S * tw;
+                if (cn < nchunks) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
+                    bulk_g2s(s_in + s * Cfg::stage_bytes, in + cn * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
+                }
+                bulk_wait_read<1>();  // staging buffer ob no longer read by the store of it-2
+            }
+        }
+        __syncwarp();
+        uint32_t *obase = INPLACE ? reinterpret_cast<uint32_t *>(s_in + s * Cfg::stage_bytes)
+                                  : reinterpret_cast<uint32_t *>(s_out + ob * Cfg::out_buf_bytes);
+        {
+            OutPacker<Cfg::GK, Cfg::ALIGNED, Cfg::V> op(obase + out_w, out_sh);
+            SynPacker<Cfg::SB, SYN != 0, G, Cfg::WIDE> sp(s_syn + ob * Cfg::syn_bytes + syn_off);
+            decode_part<N_, G, Cfg::R>(r, op, sp);
+            errs += sp.nonzero();
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            if constexpr (INPLACE) {
+                // the store issued last iteration has finished reading its stage: refill that stage
+                bulk_wait_read<0>();
+                if (it > 0) {
+                    const uint64_t cn = c - tw + (uint64_t)S * tw;
+                    if (cn < nchunks) {
+                        const int ps = (int)((it - 1) % S);
+                        mbar_arrive_expect_tx(&bar[ps], Cfg::in_bytes);
+                        bulk_g2s(s_in + ps * Cfg::stage_bytes, in + cn * (uint64_t)Cfg::in_words, Cfg::in_bytes,
+                                 &bar[ps]);
+                    }
+                }
+            }
+            bulk_s2g(out + c * (uint64_t)Cfg::out_words, obase, Cfg::out_bytes);
+            if constexpr (SYN != 0)
+                bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
+            bulk_commit();
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (aborted) {
+            atomicOr(status, (uint32_t)HD_ERR_TIMEOUT);
+            // wait (bounded) for every load still in flight into this warp's ring
+            // (in-place refills lag one iteration, so one fewer is outstanding)
+            const uint32_t pending = INPLACE ? S - 1 : S;
+            for (uint32_t j = it; j < it + pending; ++j) {
+                const uint64_t cj = gw + (uint64_t)j * tw;
+                if (cj < nchunks) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+            }
+        }
+        bulk_wait_all<0>();
+    }
+    if (err != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
+        if (lane == 0 && errs != 0) atomicAdd(err, (unsigned long long)errs);
+    }
+}
+
+template <int N_, int SYN, int T, int S, int G, int INPLACE>
+cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
+                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st);
+
+// Per-device configuration of a kernel (dynamic shared memory opt-in and the
+// number of resident CTAs per SM).
+int stream_blocks_per_sm(const void *kernel, int threads, uint32_t smem);
+
+template <int N_, int SYN, int T, int S, int G, int INPLACE>
+cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
+                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st)
+{
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
+    auto kern = k_decode_stream<N_, SYN, T, S, G, INPLACE>;
+    const int bps = stream_blocks_per_sm(reinterpret_cast<const void *>(kern), T, Cfg::smem);
+    if (bps <= 0) return cudaErrorInvalidConfiguration;
+    const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
+    const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
+    const int grid = (int)(want < cap ? want : cap);
+    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int N_, int SYN, int T, int S, int G, int INPLACE>
+StreamVariant make_variant()
+{
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
+    StreamVariant v;
+    v.n = N_;
+    v.syn = SYN;
+    v.G = G;
+    v.T = T;
+    v.S = S;
+    v.inplace = INPLACE;
+    v.smem = Cfg::smem;
+    v.chunk_cw = (uint64_t)32 * G;
+    v.launch = &launch_stream_variant<N_, SYN, T, S, G, INPLACE>;
+    v.kernel = reinterpret_cast<const void *>(k_decode_stream<N_, SYN, T, S, G, INPLACE>);
+    return v;
+}
+
+// All syndrome types of one configuration.
+template <int N_, int T, int S, int G, int INPLACE>
+void add_variants(std::vector<StreamVariant> &out)
+{
+    out.push_back(make_variant<N_, 0, T, S, G, INPLACE>());
+    out.push_back(make_variant<N_, 1, T, S, G, INPLACE>());
+    out.push_back(make_variant<N_, 2, T, S, G, INPLACE>());
+}
+
+}  // namespace hd

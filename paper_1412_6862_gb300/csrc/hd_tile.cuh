@@ -1,9 +1,12 @@
-// hd_tile.cuh -- the per-thread decode of one "thread tile": 32 consecutive
-// codewords of a compile-time length n.  32 codewords of odd length fill
-// exactly n input words and k output words, so every bit offset inside the
-// tile is a compile-time constant once the codeword loop is unrolled: each
-// codeword is pulled out with one funnel shift and its data bits are packed
-// with constant shifts, with no cross-thread exchange.
+// hd_tile.cuh -- per-thread decode of G consecutive codewords of a
+// compile-time length n ("thread part").  A team of H = 32/G threads covers one
+// 32-codeword tile: n input words and k output words (n is odd, so 32
+// codewords always fill whole words).  Sub-thread h of a team starts at bit
+// h*G*n of the tile's input and bit h*G*k of its output; it re-aligns its input
+// with one funnel shift per word so that every bit offset inside its part is a
+// compile-time constant once the codeword loop is unrolled, and it shifts its
+// output back by h*G*k mod 32 on the way out (partial words at the two ends of
+// its range are written bytewise; G >= 8 keeps them byte-aligned).
 //
 // The steps follow the decoder of Sec. II-III of the paper (checksum, error
 // detection and correction, redundancy removal, merge), restated for 32-bit
@@ -41,31 +44,58 @@ struct Pend4 {
     }
 };
 
-// Output bit packer with compile-time position: appends pieces of `len` clean
-// bits and stores each completed word (in vectors of V words when the thread's
-// output region is aligned for it).
-template <int V>
+// Store bytes [sb, eb) of v into the word at p (little-endian byte order).
+__device__ __forceinline__ void store_bytes(uint32_t *p, uint32_t v, uint32_t sb, uint32_t eb)
+{
+    if (sb == 0 && eb >= 4) {
+        *p = v;
+        return;
+    }
+    uint8_t *b = reinterpret_cast<uint8_t *>(p);
+    for (uint32_t i = sb; i < eb && i < 4; ++i) b[i] = (uint8_t)(v >> (8 * i));
+}
+
+// Output bit packer.  Appends pieces of `len` clean bits at compile-time
+// positions.  GK = total bits of the part.  With ALIGNED the part starts on a
+// word boundary (one thread per tile, or G*k a multiple of 32) and completed
+// words are stored directly, in vectors of V words; otherwise every word is
+// shifted up by the runtime offset `ob` (a multiple of 8) and the first and
+// last words of the range are stored bytewise.
+template <int GK, bool ALIGNED, int V>
 struct OutPacker {
+    static constexpr int QL = (GK + 31) / 32;  // local words
     uint32_t *dst;
-    uint32_t acc = 0;
+    uint32_t ob;
+    uint32_t acc = 0, prev = 0;
     int pos = 0;  // bits already in acc
-    int q = 0;    // index of the word acc will become
+    int q = 0;    // index of the local word acc will become
     Pend4 pend;
 
-    __device__ __forceinline__ explicit OutPacker(uint32_t *d) : dst(d) {}
+    __device__ __forceinline__ OutPacker(uint32_t *d, uint32_t off) : dst(d), ob(off) {}
 
-    __device__ __forceinline__ void store(uint32_t w)
+    __device__ __forceinline__ void emit(uint32_t w)
     {
-        if constexpr (V == 1) {
-            dst[q] = w;
-        } else {
-            pend.set(q % V, w);
-            if (q % V == V - 1) {
-                if constexpr (V == 2)
-                    *reinterpret_cast<uint2 *>(dst + q - 1) = make_uint2(pend.p0, pend.p1);
-                else
-                    *reinterpret_cast<uint4 *>(dst + q - 3) = make_uint4(pend.p0, pend.p1, pend.p2, pend.p3);
+        if constexpr (ALIGNED) {
+            if constexpr (V == 1) {
+                dst[q] = w;
+            } else {
+                pend.set(q % V, w);
+                if (q % V == V - 1) {
+                    if constexpr (V == 2)
+                        *reinterpret_cast<uint2 *>(dst + q - 1) = make_uint2(pend.p0, pend.p1);
+                    else
+                        *reinterpret_cast<uint4 *>(dst + q - 3) = make_uint4(pend.p0, pend.p1, pend.p2, pend.p3);
+                }
             }
+        } else {
+            const uint32_t g = __funnelshift_l(prev, w, ob);  // (w << ob) | (prev >> (32 - ob))
+            if (q == 0)
+                store_bytes(dst, g, ob >> 3, 4);
+            else if (q < QL - 1)
+                dst[q] = g;
+            else
+                store_bytes(dst + q, g, 0, (ob + GK - 32 * q) >> 3);
+            prev = w;
         }
         ++q;
     }
@@ -78,73 +108,98 @@ struct OutPacker {
         else
             acc |= v << pos;
         if (pos + len >= 32) {
-            store(acc);
+            emit(acc);
             acc = (pos + len > 32) ? (v >> (32 - pos)) : 0u;
             pos = pos + len - 32;
         } else {
             pos += len;
         }
     }
+
+    // Flush the last partial local word and the spill into the next word.
+    __device__ __forceinline__ void finish()
+    {
+        if (pos > 0) emit(acc);
+        if constexpr (!ALIGNED) {
+            // bits of the last local word shifted past its end land in word QL
+            const int e = (int)ob + GK - 32 * QL;
+            if (e > 0) store_bytes(dst + QL, __funnelshift_l(prev, 0u, ob), 0, (uint32_t)e >> 3);
+        }
+    }
 };
 
 // Syndrome packer: 4 (u8) or 2 (u16) syndromes per word; also counts the
 // nonzero syndromes with a carry trick on the packed word (syndromes are
-// below 2^7 for every n handled here, so a byte's bit 7 is free).
-template <int SB, bool STORE>
+// below 2^7 for u8 lanes with n <= 127 and below 2^15 for u16 lanes, so the
+// top bit of each lane is free).  For n = 255 the count uses a compare.
+template <int SB, bool STORE, int G, bool WIDE>
 struct SynPacker {
+    static constexpr int PER = SB == 1 ? 4 : 2;  // syndromes per word
+    static constexpr int WORDS = G / PER;        // words of this part
+    static constexpr int VEC = WORDS >= 4 ? 4 : WORDS;
     uint8_t *dst;
     uint32_t w = 0;
-    uint32_t cnt = 0;  // per-lane-of-word counters
+    uint32_t cnt = 0;
     Pend4 pend;
 
     __device__ __forceinline__ explicit SynPacker(uint8_t *d) : dst(d) {}
 
     __device__ __forceinline__ void put(int c, uint32_t s)
     {
-        constexpr int PER = SB == 1 ? 4 : 2;
+        if constexpr (WIDE) cnt += (s != 0u);
         const int slot = c % PER;
         if (slot == 0)
             w = s;
         else
             w |= s << (slot * 8 * SB);
         if (slot == PER - 1) {
-            if constexpr (SB == 1)
-                cnt += ((w + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
-            else
-                cnt += ((w + 0x7FFF7FFFu) >> 15) & 0x00010001u;
+            if constexpr (!WIDE) {
+                if constexpr (SB == 1)
+                    cnt += ((w + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+                else
+                    cnt += ((w + 0x7FFF7FFFu) >> 15) & 0x00010001u;
+            }
             if constexpr (STORE) {
-                const int wi = c / PER;  // word index within the thread's syndromes
-                pend.set(wi & 3, w);
-                if ((wi & 3) == 3)
-                    *reinterpret_cast<uint4 *>(dst + 16 * (wi >> 2)) =
-                        make_uint4(pend.p0, pend.p1, pend.p2, pend.p3);
+                const int wi = c / PER;  // word index within the part
+                pend.set(wi % VEC, w);
+                if (wi % VEC == VEC - 1) {
+                    uint8_t *p = dst + 4 * (wi - (VEC - 1));
+                    if constexpr (VEC == 4)
+                        *reinterpret_cast<uint4 *>(p) = make_uint4(pend.p0, pend.p1, pend.p2, pend.p3);
+                    else if constexpr (VEC == 2)
+                        *reinterpret_cast<uint2 *>(p) = make_uint2(pend.p0, pend.p1);
+                    else
+                        *reinterpret_cast<uint32_t *>(p) = pend.p0;
+                }
             }
         }
     }
 
     __device__ __forceinline__ uint32_t nonzero() const
     {
-        if constexpr (SB == 1)
+        if constexpr (WIDE)
+            return cnt;
+        else if constexpr (SB == 1)
             return (cnt * 0x01010101u) >> 24;
         else
             return (cnt & 0xFFFFu) + (cnt >> 16);
     }
 };
 
-// Position-domain word w of codeword c of the thread tile held in r[0..n-1].
-template <int N_>
-__device__ __forceinline__ uint32_t tile_y(const uint32_t (&r)[N_], int c, int w)
+// Position-domain word w of codeword c of a part held in r[0..R-1].
+template <int N_, int R>
+__device__ __forceinline__ uint32_t part_y(const uint32_t (&r)[R], int c, int w)
 {
     const int start = c * N_ - 1 + 32 * w;
     if (start < 0) return r[0] << 1;
     const int a = start >> 5, sh = start & 31;
     if (sh == 0) return r[a];
-    const uint32_t hi = (a + 1 < N_) ? r[a + 1] : 0u;
+    const uint32_t hi = (a + 1 < R) ? r[a + 1] : 0u;
     return __funnelshift_r(r[a], hi, sh);
 }
 
 template <int N_>
-__device__ __forceinline__ uint32_t tile_syndrome(const uint32_t (&y)[Code<N_>::Wy])
+__device__ __forceinline__ uint32_t part_syndrome(const uint32_t (&y)[Code<N_>::Wy])
 {
     using C = Code<N_>;
     uint32_t s = 0;
@@ -169,18 +224,18 @@ __device__ __forceinline__ uint32_t tile_syndrome(const uint32_t (&y)[Code<N_>::
     return s;
 }
 
-// Decode the thread tile r[] (32 codewords), appending the data bits to `op`
-// and the syndromes to `sp`.
-template <int N_, class OP, class SP>
-__device__ __forceinline__ void decode_thread_tile(const uint32_t (&r)[N_], OP &op, SP &sp)
+// Decode the G codewords of a part held in r[] (bit 0 of r[0] is position 1
+// of its first codeword), appending data bits to `op` and syndromes to `sp`.
+template <int N_, int G, int R, class OP, class SP>
+__device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &sp)
 {
     using C = Code<N_>;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int c = 0; c < G; ++c) {
         uint32_t y[C::Wy];
 #pragma unroll
-        for (int w = 0; w < C::Wy; ++w) y[w] = tile_y<N_>(r, c, w);
-        const uint32_t s = tile_syndrome<N_>(y);
+        for (int w = 0; w < C::Wy; ++w) y[w] = part_y<N_, R>(r, c, w);
+        const uint32_t s = part_syndrome<N_>(y);
         if constexpr (C::Wy == 1) {
             y[0] ^= 1u << s;
             uint32_t d = 0;
@@ -204,6 +259,7 @@ __device__ __forceinline__ void decode_thread_tile(const uint32_t (&r)[N_], OP &
         }
         sp.put(c, s);
     }
+    op.finish();
 }
 
 }  // namespace hd

@@ -33,8 +33,25 @@ _lib = None
 _c = ctypes
 _vp, _u32, _u64, _i32 = _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int
 
+class VariantInfo(ctypes.Structure):
+    """Mirror of hd_variant_info."""
+    _fields_ = [("index", _u32), ("n", _u32), ("syn_type", _u32), ("codewords_per_thread", _u32),
+                ("threads", _u32), ("stages", _u32), ("inplace", _u32), ("smem_bytes", _u32),
+                ("chunk_codewords", _u64), ("blocks_per_sm", _c.c_int32), ("measured_us", _c.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_VIP = _c.POINTER(VariantInfo)
+
 # name -> (restype, argtypes); every entry is declared in include/hd.h
 SIGNATURES = {
+    "hd_variant_count": (_i32, [_u32, _i32, _c.POINTER(_u32)]),
+    "hd_variant_info_get": (_i32, [_u32, _i32, _u32, _VIP]),
+    "hd_variant_select": (_i32, [_u32, _i32, _c.c_int32]),
+    "hd_variant_current": (_i32, [_u32, _i32, _VIP]),
+    "hd_autotune": (_i32, [_u32, _i32, _u64, _u32, _vp, _VIP]),
     "hd_decode": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_status_string": (_c.c_char_p, [_i32]),
@@ -95,6 +112,35 @@ def hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, 
 
 def hd_encode(data_bits, n, num_codewords, stream, cuda_stream) -> int:
     return lib().hd_encode(data_bits, n, num_codewords, stream, cuda_stream)
+
+
+def hd_variant_count(n: int, syn_type: int) -> int:
+    c = _u32(0)
+    check(lib().hd_variant_count(n, syn_type, ctypes.byref(c)), "hd_variant_count")
+    return int(c.value)
+
+
+def hd_variant_info_get(n: int, syn_type: int, ordinal: int) -> dict:
+    info = VariantInfo()
+    check(lib().hd_variant_info_get(n, syn_type, ordinal, ctypes.byref(info)), "hd_variant_info_get")
+    return info.as_dict()
+
+
+def hd_variant_select(n: int, syn_type: int, ordinal: int) -> None:
+    check(lib().hd_variant_select(n, syn_type, ordinal), "hd_variant_select")
+
+
+def hd_variant_current(n: int, syn_type: int) -> dict:
+    info = VariantInfo()
+    check(lib().hd_variant_current(n, syn_type, ctypes.byref(info)), "hd_variant_current")
+    return info.as_dict()
+
+
+def hd_autotune(n: int, syn_type: int, num_codewords: int, reps: int = 5, cuda_stream=None) -> dict:
+    info = VariantInfo()
+    check(lib().hd_autotune(n, syn_type, num_codewords, reps, _stream_handle(cuda_stream), ctypes.byref(info)),
+          "hd_autotune")
+    return info.as_dict()
 
 
 def hd_device_status() -> int:

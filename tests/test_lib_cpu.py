@@ -28,6 +28,13 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(hd.SIGNATURES) == names
 
 
+def test_variant_counts_host_only(lib):
+    for n in (7, 15, 31, 63, 127, 255):
+        for syn in (0, 1, 2):
+            assert hd.hd_variant_count(n, syn) >= 1
+    assert hd.lib().hd_variant_count(8, 0, None) in (hd.HD_ERR_NULL, hd.HD_ERR_INVALID_N)
+
+
 def test_status_strings(lib):
     for code in range(9):
         assert hd.status_string(code).startswith("HD_")
