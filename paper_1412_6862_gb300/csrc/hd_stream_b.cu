@@ -7,7 +7,7 @@ void register_stream_b(std::vector<StreamVariant> &v)
 {
     add_variants<63, 128, 3, 32, 1>(v);
     add_variants<63, 128, 2, 32, 1>(v);
-    add_variants<63, 64, 4, 32, 1>(v);
+    add_variants<63, 192, 2, 32, 1>(v);
     add_variants<63, 256, 3, 16, 1>(v);
     add_variants<63, 128, 4, 16, 1>(v);
     add_variants<63, 128, 3, 32, 0>(v);

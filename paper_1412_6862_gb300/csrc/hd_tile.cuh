@@ -31,6 +31,45 @@ __host__ __device__ constexpr uint32_t bmask(int i)
     return i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
+// Integer multiply-adds.  Multiplying by 2^t shifts left (mad.lo) or, keeping
+// the high word, shifts right by 32-t (mad.hi); adding bit fields that do not
+// overlap equals OR-ing them.  The compiler is free to issue these as shifts.
+__device__ __forceinline__ uint32_t fma_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t fma_hi(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Syndrome gather for codes whose m checksum bits come from one 32-bit word:
+// the parity counts are summed into fields of F bits, the field LSBs kept, and
+// one multiply moves LSB j (bit F*j) to bit 32-m+j.  All partial products land
+// on distinct bits, so there are no carries into the top m bits.
+template <int M>
+struct SynGather {
+    static constexpr int F = M <= 4 ? 8 : 6;
+    static constexpr uint32_t lsbs()
+    {
+        uint32_t v = 0;
+        for (int j = 0; j < M; ++j) v |= 1u << (F * j);
+        return v;
+    }
+    static constexpr uint32_t mult()
+    {
+        uint32_t v = 0;
+        for (int j = 0; j < M; ++j) v |= 1u << (32 - M + j - F * j);
+        return v;
+    }
+    static_assert(32 - M + (M - 1) - F * (M - 1) >= 0, "gather multiplier fits");
+};
+
 // Four pending words held as scalars (an array here defeats scalar
 // replacement once two packers are live and lands in local memory).
 struct Pend4 {
@@ -100,16 +139,16 @@ struct OutPacker {
         ++q;
     }
 
-    // v must have no bits at or above `len`.
+    // v must have no bits at or above `len`.  The shifts run on the FMA pipe.
     __device__ __forceinline__ void append(uint32_t v, int len)
     {
         if (pos == 0)
             acc = v;
         else
-            acc |= v << pos;
+            acc = fma_lo(v, 1u << pos, acc);  // acc | (v << pos)
         if (pos + len >= 32) {
             emit(acc);
-            acc = (pos + len > 32) ? (v >> (32 - pos)) : 0u;
+            acc = (pos + len > 32) ? fma_hi(v, 1u << pos, 0u) : 0u;  // v >> (32 - pos)
             pos = pos + len - 32;
         } else {
             pos += len;
@@ -131,7 +170,8 @@ struct OutPacker {
 // Syndrome packer: 4 (u8) or 2 (u16) syndromes per word; also counts the
 // nonzero syndromes with a carry trick on the packed word (syndromes are
 // below 2^7 for u8 lanes with n <= 127 and below 2^15 for u16 lanes, so the
-// top bit of each lane is free).  For n = 255 the count uses a compare.
+// top bit of each lane is free; a popcount of the carried top bits counts the
+// nonzero lanes).  For n = 255 with u8 lanes the count uses a compare.
 template <int SB, bool STORE, int G, bool WIDE>
 struct SynPacker {
     static constexpr int PER = SB == 1 ? 4 : 2;  // syndromes per word
@@ -151,13 +191,14 @@ struct SynPacker {
         if (slot == 0)
             w = s;
         else
-            w |= s << (slot * 8 * SB);
+            w = fma_lo(s, 1u << (slot * 8 * SB), w);  // w | (s << lane offset)
         if (slot == PER - 1) {
             if constexpr (!WIDE) {
+                // a lane is nonzero iff adding 0x7F..F carries into its top bit
                 if constexpr (SB == 1)
-                    cnt += ((w + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+                    cnt = fma_lo(__popc(fma_lo(w, 1u, 0x7F7F7F7Fu) & 0x80808080u), 1u, cnt);
                 else
-                    cnt += ((w + 0x7FFF7FFFu) >> 15) & 0x00010001u;
+                    cnt = fma_lo(__popc(fma_lo(w, 1u, 0x7FFF7FFFu) & 0x80008000u), 1u, cnt);
             }
             if constexpr (STORE) {
                 const int wi = c / PER;  // word index within the part
@@ -175,15 +216,7 @@ struct SynPacker {
         }
     }
 
-    __device__ __forceinline__ uint32_t nonzero() const
-    {
-        if constexpr (WIDE)
-            return cnt;
-        else if constexpr (SB == 1)
-            return (cnt * 0x01010101u) >> 24;
-        else
-            return (cnt & 0xFFFFu) + (cnt >> 16);
-    }
+    __device__ __forceinline__ uint32_t nonzero() const { return cnt; }
 };
 
 // Position-domain word w of codeword c of a part held in r[0..R-1].
@@ -235,14 +268,25 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
         uint32_t y[C::Wy];
 #pragma unroll
         for (int w = 0; w < C::Wy; ++w) y[w] = part_y<N_, R>(r, c, w);
-        const uint32_t s = part_syndrome<N_>(y);
         if constexpr (C::Wy == 1) {
+            // checksum: parities of y & I_i, summed into fields, gathered into
+            // the top m bits of st
+            using SG = SynGather<C::m>;
+            uint32_t pf = __popc(y[0] & qmask(N_, 0));
+#pragma unroll
+            for (int i = 1; i < C::m; ++i) pf = fma_lo(__popc(y[0] & qmask(N_, i)), 1u << (SG::F * i), pf);
+            const uint32_t st = (pf & SG::lsbs()) * SG::mult();
+            const uint32_t s = fma_hi(st, 1u << C::m, 0u);  // st >> (32 - m)
+            // correction: flip position s (s = 0 flips the unused bit 0)
             y[0] ^= 1u << s;
+            // redundancy removal: run j moves down by j + 2 bits (high product)
             uint32_t d = 0;
 #pragma unroll
-            for (int j = 1; j < C::m; ++j) d |= (y[0] >> (j + 2)) & run_mask(j);
+            for (int j = 1; j < C::m; ++j) d = fma_hi(y[0] & (run_mask(j) << (j + 2)), 1u << (30 - j), d);
             op.append(d, C::k);
+            sp.put(c, s);
         } else {
+            const uint32_t s = part_syndrome<N_>(y);
 #pragma unroll
             for (int w = 0; w < C::Wy; ++w) y[w] ^= shl_clamp(1u, s - 32u * (uint32_t)w);
             uint32_t d0 = 0;
@@ -256,8 +300,8 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
                 else
                     op.append(y[w], 32);
             }
+            sp.put(c, s);
         }
-        sp.put(c, s);
     }
     op.finish();
 }
