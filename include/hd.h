@@ -128,6 +128,74 @@ hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *
 hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,
                       hd_variant_info *chosen);
 
+/* ---------------------------------------------------------------------------
+ * Batched decode: many packets of mixed n and length in one persistent launch.
+ *
+ * Each packet is an independent stream (its own input, output and syndrome
+ * buffers, all device memory, each starting on a 16-byte boundary), decoded
+ * exactly as hd_decode() would decode it.  This is the paper's splitter /
+ * decoder / merger of Sec. II applied to many segments at once: the segments
+ * are independent, so the GPU processes them in parallel (Sec. IV-A).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const uint32_t *in;     /* device, ceil(num_codewords*n/32) words */
+    uint32_t *out;          /* device, ceil(num_codewords*k/32) words */
+    void *syndromes;        /* device, num_codewords elements, or NULL */
+    uint64_t num_codewords; /* 0 is allowed (the packet is skipped, its count is 0) */
+    uint32_t n;             /* 2^m - 1, 2 <= m <= 8 */
+    uint32_t syn_type;      /* hd_syn_type; HD_SYN_NONE requires nothing, other types a syndromes buffer */
+} hd_packet;
+
+/* A plan: the packet table turned into a device tile table, owned by the
+ * library (allocated by hd_plan_create, freed by hd_plan_destroy).  The
+ * buffers the packets point to must stay valid while the plan is launched.
+ * A plan is not thread-safe: launch it from one host thread at a time. */
+typedef struct hd_plan hd_plan;
+
+typedef struct {
+    uint32_t num_packets;
+    uint32_t num_tiles;     /* warp work items: full chunks plus ragged tails */
+    uint32_t full_tiles;
+    uint32_t warps_per_cta; /* batch-kernel configuration in use */
+    uint32_t stages;
+    uint32_t smem_bytes;
+    uint32_t variant;       /* index of the configuration, < num_variants */
+    uint32_t num_variants;
+    uint64_t codewords;     /* over all packets */
+    uint64_t in_bytes, out_bytes, syn_bytes;
+    float measured_us;      /* hd_plan_autotune's time for the best configuration, -1 if not tuned */
+} hd_plan_info;
+
+/* Validate the table (HD_ERR_INVALID_N / NULL / ALIGN / SIZE for the first bad
+ * packet) and build the plan; synchronous.  The table itself (host memory) is
+ * not referenced after the call. */
+hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan **plan);
+
+/* Decode every packet of the plan on `cuda_stream`.  err_counts: device array
+ * of num_packets elements, or NULL; element i is overwritten with packet i's
+ * number of nonzero syndromes.  The first launch (and any launch with a
+ * different err_counts pointer) records the launch as a CUDA graph; later
+ * launches replay it. */
+hd_status hd_plan_launch(hd_plan *plan, unsigned long long *err_counts, void *cuda_stream);
+
+/* Time every batch-kernel configuration on the plan's own packets (`reps`
+ * launches each, 0 = 3; output buffers are overwritten, inputs only read),
+ * keep the fastest and report it.  Synchronises the stream. */
+hd_status hd_plan_autotune(hd_plan *plan, uint32_t reps, void *cuda_stream, hd_plan_info *chosen);
+
+/* Pin batch-kernel configuration `variant` (< hd_plan_info.num_variants). */
+hd_status hd_plan_select(hd_plan *plan, uint32_t variant);
+
+hd_status hd_plan_get_info(const hd_plan *plan, hd_plan_info *info);
+
+void hd_plan_destroy(hd_plan *plan);
+
+/* One-shot batched decode: builds the device tables in stream-ordered memory
+ * (cudaMallocAsync, freed with cudaFreeAsync after the launch), decodes and
+ * overwrites err_counts (device, num_packets elements, or NULL). */
+hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
+                          void *cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *hd_status_string(hd_status status);
 

@@ -1,0 +1,559 @@
+// hd_batch.cu -- batched decode of many packets of mixed n and length in one
+// persistent launch.
+//
+// A plan turns the packet table into a device table of tiles: every packet is
+// cut into full warp chunks of 32*G codewords (G = 32 for n <= 63, 16 for
+// n = 127, 8 for n = 255, so a chunk's input is at most 8 KB) and, when its
+// length is not a multiple of that, one ragged tail tile.  Warps of a
+// persistent kernel claim tiles from an atomic counter in table order (full
+// tiles grouped by n, then the tails), prefetch S claimed tiles ahead into
+// their own shared-memory stages with 1-D bulk copies, decode full tiles with
+// the same per-warp chunk decoder as the streaming kernel, decode tails with
+// the generic warp-tile decoder straight from global memory, and add each
+// tile's nonzero-syndrome count to its packet's error counter.  Dynamic
+// claiming balances packets whose lengths span six orders of magnitude.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hd_generic.cuh"
+#include "hd_internal.h"
+#include "hd_stream.cuh"
+
+namespace hd {
+
+struct DevPacket {
+    const uint32_t *in;
+    uint32_t *out;
+    uint8_t *syn;
+    uint64_t num_cw;
+    uint64_t in_words;
+    uint64_t out_words;
+    uint32_t n;
+    uint32_t m;
+    uint32_t syn_type;
+    uint32_t pad;
+};
+
+struct DevTile {
+    uint32_t packet;
+    uint32_t count;  // codewords, | kFullTile for a whole chunk of 32*G decoded by the chunk decoder
+    uint64_t c0;     // first codeword (a multiple of 32)
+};
+
+constexpr uint32_t kFullTile = 0x80000000u;
+
+// Generic (tail) tiles are cut to at most this many codewords.
+constexpr uint64_t kTailTile = 1024;
+
+__host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 255 ? 8 : (n >= 127 ? 16 : 32); }
+
+constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest chunk input (n=255, G=8: 8160 B) + spare
+constexpr uint32_t kBatchSynBytes = 32 * 32 * 2;  // largest chunk syndromes (G=32, u16)
+
+template <int WARPS, int S>
+struct BatchCfg {
+    static constexpr uint32_t off_bar = 0;
+    static constexpr uint32_t off_claim = 64;
+    static constexpr uint32_t off_stage = 128;
+    static constexpr uint32_t off_syn = off_stage + S * kBatchStageBytes;
+    static constexpr uint32_t warp_bytes = (off_syn + 2 * kBatchSynBytes + 127) / 128 * 128;
+    static constexpr uint32_t smem = WARPS * warp_bytes;
+    static_assert(S >= 2 && S <= 8, "stages");
+    static_assert(kWarpSlotWords * 4 * 2 <= kBatchStageBytes, "generic slots fit a stage");
+    static_assert(smem <= 232448, "shared memory per CTA");
+};
+
+template <int N_, int SYN>
+__device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sbuf, int lane)
+{
+    return decode_warp_chunk<N_, SYN, batch_G(N_)>(stage, const_cast<uint32_t *>(stage), sbuf, lane);
+}
+
+template <int N_>
+__device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sbuf, int lane)
+{
+    switch (syn_type) {
+        case 1: return batch_chunk<N_, 1>(stage, sbuf, lane);
+        case 2: return batch_chunk<N_, 2>(stage, sbuf, lane);
+        default: return batch_chunk<N_, 0>(stage, sbuf, lane);
+    }
+}
+
+__device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return 32u * (uint32_t)batch_G(n); }
+
+template <int WARPS, int S>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_decode_batch(const DevPacket *__restrict__ pk, const DevTile *__restrict__ tiles, uint32_t num_tiles,
+                   uint32_t *__restrict__ counter, unsigned long long *__restrict__ err_counts,
+                   uint32_t *__restrict__ status)
+{
+    using Cfg = BatchCfg<WARPS, S>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *wbase = smem + warp * Cfg::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
+    volatile uint32_t *claim = reinterpret_cast<volatile uint32_t *>(wbase + Cfg::off_claim);
+    uint8_t *s_stage = wbase + Cfg::off_stage;
+    uint8_t *s_syn = wbase + Cfg::off_syn;
+
+    // lane 0: claim the next tile into stage s and start its load (tails load nothing)
+    auto issue = [&](int s) {
+        const uint32_t t = atomicAdd(counter, 1u);
+        claim[s] = t;
+        bool loading = false;
+        if (t < num_tiles) {
+            const DevTile tl = tiles[t];
+            const DevPacket &p = pk[tl.packet];
+            if (tl.count & kFullTile) {
+                const uint32_t bytes = chunk_codewords(p.n) * p.n / 8u;
+                mbar_arrive_expect_tx(&bar[s], bytes);
+                bulk_g2s(s_stage + s * kBatchStageBytes, p.in + tl.c0 * p.n / 32u, bytes, &bar[s]);
+                loading = true;
+            }
+        }
+        if (!loading) mbar_arrive(&bar[s]);
+    };
+
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+        for (int s = 0; s < S; ++s) issue(s);
+    }
+    __syncwarp();
+
+    uint32_t it = 0;
+    bool aborted = false;
+    for (;; ++it) {
+        const int s = (int)(it % S);
+        const bool ok = mbar_wait_bounded(&bar[s], (it / S) & 1u);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            aborted = true;
+            break;
+        }
+        const uint32_t t = claim[s];
+        if (t >= num_tiles) break;  // claims only grow: every later stage is past the end too
+        const DevTile tl = tiles[t];
+        const DevPacket p = pk[tl.packet];
+        const bool full = (tl.count & kFullTile) != 0;
+        uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * kBatchStageBytes);
+        uint8_t *sbuf = s_syn + (it & 1u) * kBatchSynBytes;
+        unsigned long long errs = 0;
+        if (full) {
+            uint32_t e = 0;
+            switch (p.n) {
+                case 7: e = batch_chunk_syn<7>(p.syn_type, stage, sbuf, lane); break;
+                case 15: e = batch_chunk_syn<15>(p.syn_type, stage, sbuf, lane); break;
+                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sbuf, lane); break;
+                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sbuf, lane); break;
+                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sbuf, lane); break;
+                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sbuf, lane); break;
+                default: break;  // the plan never makes full tiles of other lengths
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+            errs = e;
+            fence_proxy_async_smem();
+            __syncwarp();
+        } else {
+            // ragged tail: generic warp tiles, the (unloaded) stage as slot memory
+            errs = generic_decode_tiles(p.in, p.in_words, p.n, p.m, p.num_cw, tl.c0 / 32, (tl.c0 + tl.count + 31) / 32,
+                                        1, p.out, p.out_words, p.syn, (int)p.syn_type, stage, stage + kWarpSlotWords);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            // the store issued last iteration has finished reading its stage: refill that stage
+            bulk_wait_read<0>();
+            if (it > 0) issue((int)((it - 1) % S));
+            if (full) {
+                const uint32_t cw = chunk_codewords(p.n);
+                const uint32_t k = p.n - p.m;
+                bulk_s2g(p.out + tl.c0 * k / 32u, stage, cw * k / 8u);
+                if (p.syn_type != 0) {
+                    const uint32_t sb = p.syn_type == 2 ? 2u : 1u;
+                    bulk_s2g(p.syn + tl.c0 * sb, sbuf, cw * sb);
+                }
+                bulk_commit();
+            }
+            if (err_counts != nullptr && errs != 0) atomicAdd(&err_counts[tl.packet], errs);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (aborted) {
+            atomicOr(status, (uint32_t)HD_ERR_TIMEOUT);
+            for (uint32_t j = it; j < it + S - 1; ++j) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+        }
+        bulk_wait_all<0>();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct BatchVariant {
+    int warps, stages;
+    uint32_t smem;
+    const void *kernel;
+    void (*launch)(int grid, uint32_t smem, cudaStream_t st, const DevPacket *, const DevTile *, uint32_t, uint32_t *,
+                   unsigned long long *, uint32_t *);
+};
+
+template <int W, int S>
+void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevPacket *pk, const DevTile *tiles,
+                         uint32_t num_tiles, uint32_t *counter, unsigned long long *err, uint32_t *status)
+{
+    k_decode_batch<W, S><<<grid, W * 32, smem, st>>>(pk, tiles, num_tiles, counter, err, status);
+}
+
+template <int W, int S>
+BatchVariant make_batch_variant()
+{
+    BatchVariant v;
+    v.warps = W;
+    v.stages = S;
+    v.smem = BatchCfg<W, S>::smem;
+    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S>);
+    v.launch = &launch_batch_kernel<W, S>;
+    return v;
+}
+
+static const std::vector<BatchVariant> &batch_variants()
+{
+    static const std::vector<BatchVariant> v = {make_batch_variant<2, 2>(), make_batch_variant<4, 2>(),
+                                                make_batch_variant<2, 3>()};
+    return v;
+}
+
+}  // namespace hd
+
+using namespace hd;
+
+struct hd_plan {
+    int device = 0;
+    uint32_t num_packets = 0;
+    uint32_t num_tiles = 0;
+    uint32_t full_tiles = 0;
+    uint64_t codewords = 0;
+    uint64_t in_bytes = 0, out_bytes = 0, syn_bytes = 0;
+    void *dmem = nullptr;
+    DevPacket *d_pk = nullptr;
+    DevTile *d_tiles = nullptr;
+    uint32_t *d_counter = nullptr;
+    int variant = 0;
+    float tuned_us = -1.f;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long *graph_err = nullptr;
+    bool graph_ok = false;
+};
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Validate the table and build the packet and tile arrays.
+hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector<DevPacket> &pk,
+                       std::vector<DevTile> &tiles, hd_plan *stats)
+{
+    if (num_packets > 0 && table == nullptr) return HD_ERR_NULL;
+    pk.resize(num_packets);
+    std::vector<DevTile> tails;
+    uint64_t ntiles = 0;
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const hd_packet &q = table[i];
+        const int m = code_m(q.n);
+        if (m == 0) return HD_ERR_INVALID_N;
+        if (q.syn_type > 2) return HD_ERR_INVALID_ARG;
+        if (q.num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+        if (q.num_codewords > 0) {
+            if (!q.in || !q.out || (q.syn_type != 0 && !q.syndromes)) return HD_ERR_NULL;
+            if (!aligned16(q.in) || !aligned16(q.out) || (q.syn_type != 0 && !aligned16(q.syndromes)))
+                return HD_ERR_ALIGN;
+        }
+        DevPacket &d = pk[i];
+        d.in = q.in;
+        d.out = q.out;
+        d.syn = static_cast<uint8_t *>(q.syndromes);
+        d.num_cw = q.num_codewords;
+        d.n = q.n;
+        d.m = (uint32_t)m;
+        d.syn_type = q.syndromes ? q.syn_type : 0;
+        d.in_words = words_for_bits(q.num_codewords * q.n);
+        d.out_words = words_for_bits(q.num_codewords * (q.n - (uint32_t)m));
+        d.pad = 0;
+        const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
+        const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
+        ntiles += nfull + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+        if (stats) {
+            stats->codewords += q.num_codewords;
+            stats->in_bytes += (q.num_codewords * q.n + 7) / 8;
+            stats->out_bytes += (q.num_codewords * (q.n - (uint32_t)m) + 7) / 8;
+            stats->syn_bytes += q.num_codewords * (d.syn_type == 2 ? 2 : d.syn_type);
+        }
+    }
+    if (ntiles >= 0xFFFFFFF0ull) return HD_ERR_CAPACITY;
+    tiles.clear();
+    tiles.reserve(ntiles);
+    // full tiles grouped by n (long codes first), then every packet's tail
+    static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
+    for (uint32_t n : order) {
+        for (uint32_t i = 0; i < num_packets; ++i) {
+            const DevPacket &d = pk[i];
+            if (d.n != n) continue;
+            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+            // n = 3 has no chunk decoder: all its codewords take the generic path
+            const uint64_t nfull = n == 3 ? 0 : d.num_cw / chunk;
+            for (uint64_t j = 0; j < nfull; ++j) tiles.push_back(DevTile{i, (uint32_t)chunk | kFullTile, j * chunk});
+            for (uint64_t c = nfull * chunk; c < d.num_cw; c += kTailTile)
+                tails.push_back(DevTile{i, (uint32_t)std::min<uint64_t>(kTailTile, d.num_cw - c), c});
+        }
+    }
+    if (stats) stats->full_tiles = (uint32_t)tiles.size();
+    tiles.insert(tiles.end(), tails.begin(), tails.end());
+    return HD_OK;
+}
+
+int batch_grid(const BatchVariant &v, uint32_t num_tiles)
+{
+    const int bps = stream_blocks_per_sm(v.kernel, v.warps * 32, v.smem);
+    if (bps <= 0) return -1;
+    const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
+    const uint64_t want = ((uint64_t)num_tiles + v.warps - 1) / v.warps;
+    return (int)std::max<uint64_t>(1, std::min(cap, want));
+}
+
+// Resolve everything that touches device state before a (possibly captured)
+// enqueue: kernel attributes, occupancy and the status word address.
+struct LaunchGeom {
+    int grid;
+    uint32_t *status;
+};
+
+cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g)
+{
+    g->status = status_ptr();
+    if (g->status == nullptr) return cudaErrorInvalidSymbol;
+    g->grid = batch_grid(batch_variants()[p->variant], p->num_tiles);
+    return g->grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *err_counts, cudaStream_t st)
+{
+    const BatchVariant &v = batch_variants()[p->variant];
+    const int grid = g.grid;
+    uint32_t *status = g.status;
+    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (err_counts) {
+        e = cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * p->num_packets, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->num_tiles == 0) return cudaSuccess;
+    v.launch(grid, v.smem, st, p->d_pk, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status);
+    return cudaGetLastError();
+}
+
+void drop_graph(hd_plan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+    p->graph_ok = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan **out)
+{
+    if (!out) return HD_ERR_NULL;
+    *out = nullptr;
+    hd_plan *p = new (std::nothrow) hd_plan();
+    if (!p) return HD_ERR_CAPACITY;
+    std::vector<DevPacket> pk;
+    std::vector<DevTile> tiles;
+    hd_status rc = build_tables(table, num_packets, pk, tiles, p);
+    if (rc != HD_OK) {
+        delete p;
+        return rc;
+    }
+    cudaGetDevice(&p->device);
+    p->num_packets = num_packets;
+    p->num_tiles = (uint32_t)tiles.size();
+    const size_t pk_b = (pk.size() * sizeof(DevPacket) + 255) / 256 * 256;
+    const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
+    if (cudaMalloc(&p->dmem, pk_b + tl_b + 256) != cudaSuccess) {
+        delete p;
+        return HD_ERR_CUDA;
+    }
+    p->d_pk = static_cast<DevPacket *>(p->dmem);
+    p->d_tiles = reinterpret_cast<DevTile *>(static_cast<char *>(p->dmem) + pk_b);
+    p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + pk_b + tl_b);
+    if ((!pk.empty() && cudaMemcpy(p->d_pk, pk.data(), pk.size() * sizeof(DevPacket), cudaMemcpyHostToDevice) !=
+                            cudaSuccess) ||
+        (!tiles.empty() &&
+         cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(p->dmem);
+        delete p;
+        return HD_ERR_CUDA;
+    }
+    *out = p;
+    return HD_OK;
+}
+
+hd_status hd_plan_launch(hd_plan *p, unsigned long long *err_counts, void *cuda_stream)
+{
+    if (!p) return HD_ERR_NULL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (!p->graph_ok || p->graph_err != err_counts) {
+        drop_graph(p);
+        LaunchGeom geom;
+        if (prepare_plan(p, &geom) != cudaSuccess) return HD_ERR_CUDA;
+        if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HD_ERR_CUDA;
+        const cudaError_t e = enqueue_plan(p, geom, err_counts, p->capture);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(p->capture, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || g == nullptr) {
+            if (g) cudaGraphDestroy(g);
+            return HD_ERR_CUDA;
+        }
+        p->graph = g;
+        if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+            drop_graph(p);
+            return HD_ERR_CUDA;
+        }
+        p->graph_err = err_counts;
+        p->graph_ok = true;
+    }
+    if (cudaGraphLaunch(p->exec, st) != cudaSuccess) return HD_ERR_CUDA;
+    if (p->num_tiles) count_launch();
+    return HD_OK;
+}
+
+hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan_info *chosen)
+{
+    if (!p) return HD_ERR_NULL;
+    if (reps == 0) reps = 3;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HD_ERR_CUDA;
+    int best = -1;
+    float best_us = 0.f;
+    const int keep = p->variant;
+    hd_status rc = HD_OK;
+    for (size_t i = 0; i < batch_variants().size(); ++i) {
+        p->variant = (int)i;
+        LaunchGeom geom;
+        if (prepare_plan(p, &geom) != cudaSuccess) continue;
+        if (enqueue_plan(p, geom, nullptr, st) != cudaSuccess) {
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        cudaEventRecord(e0, st);
+        for (uint32_t r = 0; r < reps; ++r) enqueue_plan(p, geom, nullptr, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = ms * 1000.f / (float)reps;
+        if (best < 0 || us < best_us) {
+            best = (int)i;
+            best_us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->variant = best >= 0 ? best : keep;
+    p->tuned_us = best >= 0 ? best_us : -1.f;
+    drop_graph(p);
+    if (rc != HD_OK) return rc;
+    if (chosen) return hd_plan_get_info(p, chosen);
+    return HD_OK;
+}
+
+hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
+{
+    if (!p || !info) return HD_ERR_NULL;
+    std::memset(info, 0, sizeof(*info));
+    const BatchVariant &v = batch_variants()[p->variant];
+    info->num_packets = p->num_packets;
+    info->num_tiles = p->num_tiles;
+    info->full_tiles = p->full_tiles;
+    info->codewords = p->codewords;
+    info->in_bytes = p->in_bytes;
+    info->out_bytes = p->out_bytes;
+    info->syn_bytes = p->syn_bytes;
+    info->warps_per_cta = (uint32_t)v.warps;
+    info->stages = (uint32_t)v.stages;
+    info->smem_bytes = v.smem;
+    info->variant = (uint32_t)p->variant;
+    info->num_variants = (uint32_t)batch_variants().size();
+    info->measured_us = p->tuned_us;
+    return HD_OK;
+}
+
+hd_status hd_plan_select(hd_plan *p, uint32_t variant)
+{
+    if (!p) return HD_ERR_NULL;
+    if (variant >= batch_variants().size()) return HD_ERR_INVALID_ARG;
+    p->variant = (int)variant;
+    drop_graph(p);
+    return HD_OK;
+}
+
+void hd_plan_destroy(hd_plan *p)
+{
+    if (!p) return;
+    drop_graph(p);
+    if (p->capture) cudaStreamDestroy(p->capture);
+    if (p->dmem) cudaFree(p->dmem);
+    delete p;
+}
+
+hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
+                          void *cuda_stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<DevPacket> pk;
+    std::vector<DevTile> tiles;
+    hd_plan p;
+    hd_status rc = build_tables(table, num_packets, pk, tiles, &p);
+    if (rc != HD_OK) return rc;
+    p.num_packets = num_packets;
+    p.num_tiles = (uint32_t)tiles.size();
+    const size_t pk_b = (pk.size() * sizeof(DevPacket) + 255) / 256 * 256;
+    const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
+    // stream-ordered scratch: freed on the stream once the kernel has run
+    if (cudaMallocAsync(&p.dmem, pk_b + tl_b + 256, st) != cudaSuccess) return HD_ERR_CUDA;
+    p.d_pk = static_cast<DevPacket *>(p.dmem);
+    p.d_tiles = reinterpret_cast<DevTile *>(static_cast<char *>(p.dmem) + pk_b);
+    p.d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p.dmem) + pk_b + tl_b);
+    // pageable sources: the copies have read the host vectors when these calls return
+    if ((!pk.empty() && cudaMemcpyAsync(p.d_pk, pk.data(), pk.size() * sizeof(DevPacket), cudaMemcpyHostToDevice,
+                                        st) != cudaSuccess) ||
+        (!tiles.empty() && cudaMemcpyAsync(p.d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+        cudaFreeAsync(p.dmem, st);
+        return HD_ERR_CUDA;
+    }
+    LaunchGeom geom;
+    cudaError_t e = prepare_plan(&p, &geom);
+    if (e == cudaSuccess) e = enqueue_plan(&p, geom, err_counts, st);
+    if (p.num_tiles && e == cudaSuccess) count_launch();
+    cudaFreeAsync(p.dmem, st);
+    p.dmem = nullptr;
+    return e == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+}  // extern "C"

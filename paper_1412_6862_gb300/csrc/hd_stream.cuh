@@ -38,44 +38,84 @@ struct StreamVariant {
     const void *kernel;
 };
 
+// Geometry of one warp chunk of code n: 32*G codewords, G tiles of 32.
+template <int N_, int SYN, int G>
+struct ChunkGeom {
+    using C = Code<N_>;
+    static constexpr int H = 32 / G;                      // threads per 32-codeword tile
+    static constexpr int TEAMS = G;                       // tiles per warp chunk
+    static constexpr int SB = SYN == 2 ? 2 : 1;           // syndrome bytes (packing width)
+    static constexpr bool WIDE = (SB == 1 && C::m == 8);  // u8 lanes may use bit 7
+    static constexpr int GK = G * C::k;                   // output bits per thread
+    static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
+    static constexpr int R = (G * N_ + 31) / 32;          // input words per thread after re-alignment
+    static constexpr uint32_t in_words = TEAMS * N_;
+    static constexpr uint32_t in_bytes = in_words * 4;
+    static constexpr uint32_t out_words = TEAMS * C::k;
+    static constexpr uint32_t out_bytes = out_words * 4;
+    static constexpr uint32_t syn_bytes = SYN ? 32 * G * SB : 0;
+    static constexpr int V = !ALIGNED                                ? 1
+                             : (C::k % 4 == 0 && (GK / 32) % 4 == 0) ? 4
+                             : (C::k % 2 == 0 && (GK / 32) % 2 == 0) ? 2
+                                                                     : 1;
+    static_assert(in_bytes % 16 == 0 && out_bytes % 16 == 0 && syn_bytes % 16 == 0, "bulk copies need 16B sizes");
+};
+
+// Decode one warp chunk held in shared memory at `stage` (its input words,
+// plus one spare word).  Writes the chunk's output words at `obase` (which may
+// equal `stage`: every lane copies its part to registers and the warp
+// synchronises before the first write) and its syndromes at `sbase`.  Returns
+// this lane's count of nonzero syndromes.
+template <int N_, int SYN, int G>
+__device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uint32_t *obase, uint8_t *sbase, int lane)
+{
+    using Q = ChunkGeom<N_, SYN, G>;
+    constexpr int H = Q::H;
+    const int team = lane / H, h = lane % H;
+    const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * N_);
+    const uint32_t in_w = team * N_ + (in_bit >> 5), in_sh = in_bit & 31u;
+    const uint32_t out_bit = (uint32_t)h * (uint32_t)Q::GK;
+    const uint32_t out_w = team * Code<N_>::k + (out_bit >> 5), out_sh = out_bit & 31u;
+    uint32_t r[Q::R];
+    if constexpr (H == 1) {
+#pragma unroll
+        for (int w = 0; w < Q::R; ++w) r[w] = stage[in_w + w];
+    } else {
+        uint32_t lo = stage[in_w];
+#pragma unroll
+        for (int w = 0; w < Q::R; ++w) {
+            const uint32_t hi = stage[in_w + w + 1];
+            r[w] = __funnelshift_r(lo, hi, in_sh);
+            lo = hi;
+        }
+    }
+    __syncwarp();  // the whole chunk is in registers
+    OutPacker<Q::GK, Q::ALIGNED, Q::V> op(obase + out_w, out_sh);
+    SynPacker<Q::SB, SYN != 0, G, Q::WIDE> sp(sbase + (uint32_t)lane * G * Q::SB);
+    decode_part<N_, G, Q::R>(r, op, sp);
+    return sp.nonzero();
+}
+
 // Every warp is an independent pipeline: it owns S input stages with one
 // mbarrier each, (unless INPLACE) two output staging buffers, and two syndrome
 // buffers.  Lane 0 issues the warp's bulk loads and stores; warps never wait
 // for one another, so one warp's memory wait overlaps the others' arithmetic.
 template <int N_, int SYN, int T, int S, int G, int INPLACE>
-struct StreamCfg {
-    using C = Code<N_>;
+struct StreamCfg : ChunkGeom<N_, SYN, G> {
+    using Q = ChunkGeom<N_, SYN, G>;
     static constexpr int WARPS = T / 32;
-    static constexpr int H = 32 / G;                       // threads per 32-codeword tile
-    static constexpr int TEAMS = 32 / H;                   // tiles per warp chunk
-    static constexpr int SB = SYN == 2 ? 2 : 1;            // syndrome bytes (packing width)
-    static constexpr bool WIDE = (SB == 1 && C::m == 8);   // u8 lanes may use bit 7
-    static constexpr int GK = G * C::k;                    // output bits per thread
-    static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
-    static constexpr int R = (G * N_ + 31) / 32;           // input words per thread after re-alignment
-    static constexpr uint32_t in_words = TEAMS * N_;       // per warp chunk
-    static constexpr uint32_t in_bytes = in_words * 4;
-    static constexpr uint32_t stage_bytes = in_bytes + 16;  // one spare 16-byte group for the funnel read
-    static constexpr uint32_t out_words = TEAMS * C::k;
-    static constexpr uint32_t out_bytes = out_words * 4;
-    static constexpr uint32_t out_buf_bytes = (out_bytes + 15) / 16 * 16 + 16;  // room for the last spill word
-    static constexpr uint32_t syn_bytes = SYN ? 32 * G * SB : 0;
+    static constexpr uint32_t stage_bytes = Q::in_bytes + 16;  // one spare 16-byte group for the funnel read
+    static constexpr uint32_t out_buf_bytes = Q::out_bytes + 16;  // room for a spill word
     // per-warp layout
     static constexpr uint32_t off_bar = 0;
     static constexpr uint32_t off_in = 64;
     static constexpr uint32_t off_out = off_in + S * stage_bytes;
     static constexpr uint32_t off_syn = off_out + (INPLACE ? 0 : 2 * out_buf_bytes);
-    static constexpr uint32_t warp_bytes = (off_syn + 2 * syn_bytes + 127) / 128 * 128;
+    static constexpr uint32_t warp_bytes = (off_syn + 2 * Q::syn_bytes + 127) / 128 * 128;
     static constexpr uint32_t smem = WARPS * warp_bytes;
-    static constexpr int V = !ALIGNED                                ? 1
-                             : (C::k % 4 == 0 && (GK / 32) % 4 == 0) ? 4
-                             : (C::k % 2 == 0 && (GK / 32) % 2 == 0) ? 2
-                                                                     : 1;
     static_assert(T % 32 == 0 && S <= 8, "whole warps, at most 8 stages");
-    static_assert(in_bytes % 16 == 0 && out_bytes % 16 == 0 && syn_bytes % 16 == 0, "bulk copies need 16B sizes");
-    static_assert(stage_bytes % 16 == 0 && out_buf_bytes % 16 == 0, "16B-aligned buffers");
     static_assert(smem <= 232448, "shared memory per CTA");
-    static_assert(!INPLACE || out_bytes + 16 <= stage_bytes, "in-place output fits the input stage");
+    static_assert(!INPLACE || Q::out_bytes + 16 <= stage_bytes, "in-place output fits the input stage");
     static_assert(!INPLACE || S >= 2, "in-place refills lag one iteration");
 };
 
@@ -85,9 +125,6 @@ __global__ void __launch_bounds__(T)
                     unsigned long long *__restrict__ err, uint32_t *__restrict__ status, uint64_t nchunks)
 {
     using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
-    using C = Code<N_>;
-    constexpr int K = C::k;
-    constexpr int H = Cfg::H;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * Cfg::warp_bytes;
@@ -95,13 +132,6 @@ __global__ void __launch_bounds__(T)
     uint8_t *s_in = wbase + Cfg::off_in;
     uint8_t *s_out = wbase + Cfg::off_out;
     uint8_t *s_syn = wbase + Cfg::off_syn;
-    const int team = lane / H, h = lane % H;
-    // this thread's part inside its tile
-    const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * N_);
-    const uint32_t in_w = team * N_ + (in_bit >> 5), in_sh = in_bit & 31u;
-    const uint32_t out_bit = (uint32_t)h * (uint32_t)Cfg::GK;
-    const uint32_t out_w = team * K + (out_bit >> 5), out_sh = out_bit & 31u;
-    const uint32_t syn_off = (uint32_t)lane * G * Cfg::SB;
     const uint64_t gw = (uint64_t)blockIdx.x * Cfg::WARPS + warp;  // global warp index
     const uint64_t tw = (uint64_t)gridDim.x * Cfg::WARPS;          // warps in the grid
 
@@ -132,42 +162,14 @@ __global__ void __launch_bounds__(T)
             aborted = true;
             break;
         }
+        if constexpr (!INPLACE) {
+            if (lane == 0) bulk_wait_read<1>();  // staging buffer ob no longer read by the store of it-2
+            __syncwarp();
+        }
         const uint32_t *stage = reinterpret_cast<const uint32_t *>(s_in + s * Cfg::stage_bytes);
-        uint32_t r[Cfg::R];
-        if constexpr (H == 1) {
-#pragma unroll
-            for (int w = 0; w < Cfg::R; ++w) r[w] = stage[in_w + w];
-        } else {
-            uint32_t lo = stage[in_w];
-#pragma unroll
-            for (int w = 0; w < Cfg::R; ++w) {
-                const uint32_t hi = stage[in_w + w + 1];
-                r[w] = __funnelshift_r(lo, hi, in_sh);
-                lo = hi;
-            }
-        }
-        __syncwarp();  // the whole chunk is in registers
-        if (lane == 0) {
-            if constexpr (!INPLACE) {
-                // the stage is free again: prefetch the chunk S iterations ahead into it
-                const uint64_t cn = c + (uint64_t)S * tw;
-                if (cn < nchunks) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
-                    bulk_g2s(s_in + s * Cfg::stage_bytes, in + cn * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
-                }
-                bulk_wait_read<1>();  // staging buffer ob no longer read by the store of it-2
-            }
-        }
-        __syncwarp();
         uint32_t *obase = INPLACE ? reinterpret_cast<uint32_t *>(s_in + s * Cfg::stage_bytes)
                                   : reinterpret_cast<uint32_t *>(s_out + ob * Cfg::out_buf_bytes);
-        {
-            OutPacker<Cfg::GK, Cfg::ALIGNED, Cfg::V> op(obase + out_w, out_sh);
-            SynPacker<Cfg::SB, SYN != 0, G, Cfg::WIDE> sp(s_syn + ob * Cfg::syn_bytes + syn_off);
-            decode_part<N_, G, Cfg::R>(r, op, sp);
-            errs += sp.nonzero();
-        }
+        errs += decode_warp_chunk<N_, SYN, G>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -188,6 +190,14 @@ __global__ void __launch_bounds__(T)
             if constexpr (SYN != 0)
                 bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
             bulk_commit();
+            if constexpr (!INPLACE) {
+                // the stage was consumed by this iteration: prefetch the chunk S iterations ahead
+                const uint64_t cn = c + (uint64_t)S * tw;
+                if (cn < nchunks) {
+                    mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
+                    bulk_g2s(s_in + s * Cfg::stage_bytes, in + cn * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
+                }
+            }
         }
         __syncwarp();
     }

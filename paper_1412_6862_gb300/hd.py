@@ -45,6 +45,27 @@ class VariantInfo(ctypes.Structure):
 
 _VIP = _c.POINTER(VariantInfo)
 
+
+class Packet(ctypes.Structure):
+    """Mirror of hd_packet."""
+    _fields_ = [("in_", _vp), ("out", _vp), ("syndromes", _vp), ("num_codewords", _u64), ("n", _u32),
+                ("syn_type", _u32)]
+
+
+class PlanInfo(ctypes.Structure):
+    """Mirror of hd_plan_info."""
+    _fields_ = [("num_packets", _u32), ("num_tiles", _u32), ("full_tiles", _u32), ("warps_per_cta", _u32),
+                ("stages", _u32), ("smem_bytes", _u32), ("variant", _u32), ("num_variants", _u32),
+                ("codewords", _u64), ("in_bytes", _u64), ("out_bytes", _u64), ("syn_bytes", _u64),
+                ("measured_us", _c.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_PKP = _c.POINTER(Packet)
+_PIP = _c.POINTER(PlanInfo)
+
 # name -> (restype, argtypes); every entry is declared in include/hd.h
 SIGNATURES = {
     "hd_variant_count": (_i32, [_u32, _i32, _c.POINTER(_u32)]),
@@ -53,6 +74,13 @@ SIGNATURES = {
     "hd_variant_current": (_i32, [_u32, _i32, _VIP]),
     "hd_autotune": (_i32, [_u32, _i32, _u64, _u32, _vp, _VIP]),
     "hd_decode": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp]),
+    "hd_plan_create": (_i32, [_PKP, _u32, _c.POINTER(_vp)]),
+    "hd_plan_launch": (_i32, [_vp, _vp, _vp]),
+    "hd_plan_autotune": (_i32, [_vp, _u32, _vp, _PIP]),
+    "hd_plan_select": (_i32, [_vp, _u32]),
+    "hd_plan_get_info": (_i32, [_vp, _PIP]),
+    "hd_plan_destroy": (None, [_vp]),
+    "hd_decode_batch": (_i32, [_PKP, _u32, _vp, _vp]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -141,6 +169,83 @@ def hd_autotune(n: int, syn_type: int, num_codewords: int, reps: int = 5, cuda_s
     check(lib().hd_autotune(n, syn_type, num_codewords, reps, _stream_handle(cuda_stream), ctypes.byref(info)),
           "hd_autotune")
     return info.as_dict()
+
+
+def packet_table(packets) -> ctypes.Array:
+    """ctypes array of hd_packet from (in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type) tuples."""
+    arr = (Packet * max(1, len(packets)))()
+    for i, (a, b, c, N, n, st) in enumerate(packets):
+        arr[i] = Packet(a, b, c, N, n, st)
+    return arr
+
+
+def hd_plan_create(table, num_packets: int) -> int:
+    plan = _vp()
+    check(lib().hd_plan_create(table, num_packets, ctypes.byref(plan)), "hd_plan_create")
+    return plan.value
+
+
+def hd_plan_launch(plan: int, err_counts, cuda_stream) -> int:
+    return lib().hd_plan_launch(plan, err_counts, cuda_stream)
+
+
+def hd_plan_autotune(plan: int, reps: int = 3, cuda_stream=None) -> dict:
+    info = PlanInfo()
+    check(lib().hd_plan_autotune(plan, reps, _stream_handle(cuda_stream), ctypes.byref(info)), "hd_plan_autotune")
+    return info.as_dict()
+
+
+def hd_plan_select(plan: int, variant: int) -> None:
+    check(lib().hd_plan_select(plan, variant), "hd_plan_select")
+
+
+def hd_plan_get_info(plan: int) -> dict:
+    info = PlanInfo()
+    check(lib().hd_plan_get_info(plan, ctypes.byref(info)), "hd_plan_get_info")
+    return info.as_dict()
+
+
+def hd_plan_destroy(plan: int) -> None:
+    lib().hd_plan_destroy(plan)
+
+
+def hd_decode_batch(table, num_packets: int, err_counts, cuda_stream) -> int:
+    return lib().hd_decode_batch(table, num_packets, err_counts, cuda_stream)
+
+
+class Plan:
+    """A batched-decode plan over device tensors.  ``packets`` holds
+    (in, out, syndromes or None, num_codewords, n, syn_type) with tensors."""
+
+    def __init__(self, packets):
+        self._keep = packets
+        self.table = packet_table([(_ptr(a), _ptr(b), _ptr(c), N, n, st if c is not None else SYN_NONE)
+                                   for a, b, c, N, n, st in packets])
+        self.handle = hd_plan_create(self.table, len(packets))
+        self.num_packets = len(packets)
+
+    def launch(self, err_counts=None, cuda_stream=None) -> None:
+        check(hd_plan_launch(self.handle, _ptr(err_counts), _stream_handle(cuda_stream)), "hd_plan_launch")
+
+    def autotune(self, reps: int = 3, cuda_stream=None) -> dict:
+        return hd_plan_autotune(self.handle, reps, cuda_stream)
+
+    def select(self, variant: int) -> None:
+        hd_plan_select(self.handle, variant)
+
+    def info(self) -> dict:
+        return hd_plan_get_info(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            hd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hd_device_status() -> int:

@@ -67,3 +67,18 @@ def test_no_launches_counted_for_rejected_calls(lib):
     before = hd.hd_launch_count()
     hd.hd_decode(16, 7 * 4 + 1, 7, 4, 16, None, 0, None, None)
     assert hd.hd_launch_count() == before
+
+
+def test_plan_validation_host_only(lib):
+    import ctypes
+    bad_n = hd.packet_table([(16, 16, None, 10, 8, 0)])
+    plan = ctypes.c_void_p()
+    assert hd.lib().hd_plan_create(bad_n, 1, ctypes.byref(plan)) == hd.HD_ERR_INVALID_N
+    misaligned = hd.packet_table([(16, 16, None, 10, 7, 0), (20, 16, None, 10, 7, 0)])
+    assert hd.lib().hd_plan_create(misaligned, 2, ctypes.byref(plan)) == hd.HD_ERR_ALIGN
+    null_in = hd.packet_table([(None, 16, None, 10, 15, 0)])
+    assert hd.lib().hd_plan_create(null_in, 1, ctypes.byref(plan)) == hd.HD_ERR_NULL
+    null_syn = hd.packet_table([(16, 16, None, 10, 15, 1)])
+    assert hd.lib().hd_plan_create(null_syn, 1, ctypes.byref(plan)) == hd.HD_ERR_NULL
+    assert hd.lib().hd_plan_create(None, 3, ctypes.byref(plan)) == hd.HD_ERR_NULL
+    assert hd.lib().hd_decode_batch(bad_n, 1, None, None) == hd.HD_ERR_INVALID_N
