@@ -196,6 +196,31 @@ void hd_plan_destroy(hd_plan *plan);
 hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
                           void *cuda_stream);
 
+/* Batched decode that allocates nothing.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory: a process
+ * that budgets all device memory up front, an application whose allocator
+ * hooks forbid allocations from inside libraries, or a latency-critical
+ * receive path where an allocation could stall or fail.  It decodes exactly
+ * like hd_decode_batch(), but its packet table, tile table and claim counter
+ * live in one fixed 1 MiB array compiled into libhd.so; every device that
+ * loads the library holds that array until the process exits.
+ *
+ * Limits: at most 4096 packets and 49,136 tiles (a tile is a chunk of 256 to
+ * 1024 codewords, or up to 1024 codewords of a packet's tail); larger batches
+ * return HD_ERR_CAPACITY before anything is enqueued.
+ * First call on a device: performs a one-time set-up (it looks up the array's
+ * device address and the kernel's launch attributes); make that first call
+ * before any stream capture.
+ * Every call reuses the same array, which keeps the previous call's tables:
+ * the claim counter is cleared on `cuda_stream` at the start of each call,
+ * and two calls that overlap on the GPU (for example on two streams) race on
+ * the array, so order them on one stream or synchronise between them.  The
+ * tables are copied from pageable host memory, so the call waits for earlier
+ * work on `cuda_stream` before it returns.  Calls from several host threads
+ * are serialised.  err_counts is overwritten as in hd_decode_batch(). */
+hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
+                                  void *cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *hd_status_string(hd_status status);
 

@@ -557,3 +557,145 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched decode without allocation.
+//
+// For callers that must not allocate device memory -- a process that budgets
+// every byte of device memory up front, an application whose allocator hooks
+// forbid allocations from inside libraries, or a latency-critical receive
+// path where an allocation could stall or fail -- the packet table, the tile
+// table and the claim counter of the batched decoder live in one fixed array
+// compiled into this library.  The array is kNoAllocBytes (1 MiB) on every
+// device that loads the library and stays there until the process exits.
+// ---------------------------------------------------------------------------
+namespace hd {
+namespace {
+
+constexpr uint32_t kNoAllocBytes = 1u << 20;
+constexpr uint32_t kNoAllocMaxPackets = 4096;
+constexpr uint32_t kNoAllocPacketsOff = 256;  // the claim counter sits at offset 0
+constexpr uint32_t kNoAllocTilesOff = kNoAllocPacketsOff + kNoAllocMaxPackets * sizeof(DevPacket);
+constexpr uint32_t kNoAllocMaxTiles = (kNoAllocBytes - kNoAllocTilesOff) / sizeof(DevTile);
+static_assert(sizeof(DevPacket) == 64 && sizeof(DevTile) == 16, "table layout");
+
+// The device scratch.  In host code this name is only a handle for
+// cudaGetSymbolAddress; kernels receive the device address it returns.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host image of the tables, uploaded with one copy per table.  The copies read
+// pageable memory, so they have consumed it when cudaMemcpyAsync returns and
+// the next call may rewrite it; the mutex serialises host threads.
+alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char *g_noalloc_dev[kNoAllocMaxDevices];  // device address of the scratch, per device
+uint32_t *g_noalloc_status[kNoAllocMaxDevices];
+
+// One-time set-up on the current device: the scratch array's device address,
+// the status word and the kernel's launch attributes.
+hd_status noalloc_setup(int dev)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return HD_ERR_CAPACITY;
+    if (g_noalloc_dev[dev] != nullptr) return HD_OK;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return HD_ERR_CUDA;
+    uint32_t *status = status_ptr();
+    if (status == nullptr) return HD_ERR_CUDA;
+    const BatchVariant &v = batch_variants()[0];
+    if (stream_blocks_per_sm(v.kernel, v.warps * 32, v.smem) <= 0) return HD_ERR_CUDA;
+    g_noalloc_status[dev] = status;
+    g_noalloc_dev[dev] = static_cast<unsigned char *>(p);
+    return HD_OK;
+}
+
+}  // namespace
+}  // namespace hd
+
+extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets,
+                                             unsigned long long *err_counts, void *cuda_stream)
+{
+    if (num_packets > 0 && table == nullptr) return HD_ERR_NULL;
+    if (num_packets > kNoAllocMaxPackets) return HD_ERR_CAPACITY;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HD_ERR_CUDA;
+    // validate and count tiles before touching anything
+    uint64_t ntiles = 0;
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const hd_packet &q = table[i];
+        const int m = code_m(q.n);
+        if (m == 0) return HD_ERR_INVALID_N;
+        if (q.syn_type > 2) return HD_ERR_INVALID_ARG;
+        if (q.num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+        if (q.num_codewords > 0) {
+            if (!q.in || !q.out || (q.syn_type != 0 && !q.syndromes)) return HD_ERR_NULL;
+            if (!aligned16(q.in) || !aligned16(q.out) || (q.syn_type != 0 && !aligned16(q.syndromes)))
+                return HD_ERR_ALIGN;
+        }
+        const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
+        const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
+        ntiles += nfull + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+    }
+    if (ntiles > kNoAllocMaxTiles) return HD_ERR_CAPACITY;
+    const hd_status su = noalloc_setup(dev);
+    if (su != HD_OK) return su;
+    unsigned char *dbase = g_noalloc_dev[dev];
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    // host image: packets, then full tiles grouped by n (long codes first), then tails
+    DevPacket *hp = reinterpret_cast<DevPacket *>(g_noalloc_host + kNoAllocPacketsOff);
+    DevTile *ht = reinterpret_cast<DevTile *>(g_noalloc_host + kNoAllocTilesOff);
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const hd_packet &q = table[i];
+        const uint32_t m = (uint32_t)code_m(q.n);
+        DevPacket &d = hp[i];
+        d.in = q.in;
+        d.out = q.out;
+        d.syn = static_cast<uint8_t *>(q.syndromes);
+        d.num_cw = q.num_codewords;
+        d.n = q.n;
+        d.m = m;
+        d.syn_type = q.syndromes ? q.syn_type : 0;
+        d.in_words = words_for_bits(q.num_codewords * q.n);
+        d.out_words = words_for_bits(q.num_codewords * (q.n - m));
+        d.pad = 0;
+    }
+    uint32_t t = 0;
+    static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
+    for (uint32_t n : order)
+        for (uint32_t i = 0; i < num_packets; ++i) {
+            if (hp[i].n != n || n == 3) continue;
+            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+            for (uint64_t j = 0; j < hp[i].num_cw / chunk; ++j) ht[t++] = DevTile{i, (uint32_t)chunk | kFullTile, j * chunk};
+        }
+    for (uint32_t n : order)
+        for (uint32_t i = 0; i < num_packets; ++i) {
+            if (hp[i].n != n) continue;
+            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+            const uint64_t first = n == 3 ? 0 : hp[i].num_cw / chunk * chunk;
+            for (uint64_t c = first; c < hp[i].num_cw; c += kTailTile)
+                ht[t++] = DevTile{i, (uint32_t)std::min<uint64_t>(kTailTile, hp[i].num_cw - c), c};
+        }
+
+    // the claim counter must start at zero; the error counters are overwritten
+    uint32_t *counter = reinterpret_cast<uint32_t *>(dbase);
+    if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess) return HD_ERR_CUDA;
+    if (err_counts && num_packets &&
+        cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * num_packets, st) != cudaSuccess)
+        return HD_ERR_CUDA;
+    if (t == 0) return HD_OK;
+    if (cudaMemcpyAsync(dbase + kNoAllocPacketsOff, hp, sizeof(DevPacket) * num_packets, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dbase + kNoAllocTilesOff, ht, sizeof(DevTile) * t, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return HD_ERR_CUDA;
+    const BatchVariant &v = batch_variants()[0];
+    const int grid = batch_grid(v, t);
+    if (grid <= 0) return HD_ERR_CUDA;
+    v.launch(grid, v.smem, st, reinterpret_cast<const DevPacket *>(dbase + kNoAllocPacketsOff),
+             reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
+             g_noalloc_status[dev]);
+    if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
+    count_launch();
+    return HD_OK;
+}

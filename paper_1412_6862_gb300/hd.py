@@ -81,6 +81,7 @@ SIGNATURES = {
     "hd_plan_get_info": (_i32, [_vp, _PIP]),
     "hd_plan_destroy": (None, [_vp]),
     "hd_decode_batch": (_i32, [_PKP, _u32, _vp, _vp]),
+    "hd_decode_batch_noalloc": (_i32, [_PKP, _u32, _vp, _vp]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -211,6 +212,10 @@ def hd_plan_destroy(plan: int) -> None:
 
 def hd_decode_batch(table, num_packets: int, err_counts, cuda_stream) -> int:
     return lib().hd_decode_batch(table, num_packets, err_counts, cuda_stream)
+
+
+def hd_decode_batch_noalloc(table, num_packets: int, err_counts, cuda_stream) -> int:
+    return lib().hd_decode_batch_noalloc(table, num_packets, err_counts, cuda_stream)
 
 
 class Plan:
