@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--codes", type=str, default=",".join(map(str, SWEEP_CODES)),
                     help="subset of the sweep codes to run (profiling a single kernel)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched mixed-n section")
+    ap.add_argument("--batched-only", action="store_true", help="run only the batched mixed-n section")
+    ap.add_argument("--batched-packets", type=int, default=10000)
+    ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -226,6 +230,132 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched mixed-n workload
+# ---------------------------------------------------------------------------
+BATCH_P1 = 0.05
+
+
+def align4(w):
+    return (w + 3) // 4 * 4
+
+
+def build_batched(dev, num_packets, seed=0, lengths=None):
+    """The batched configuration: packets with n uniform over the six codes (or
+    over ``lengths``) and log-uniform lengths, every buffer 16-byte aligned
+    inside three arenas.  Codewords come from the GPU encoder; channel errors
+    from the generator."""
+    import torch
+    from paper_1412_6862_gb300 import hd, synth
+    specs = synth.packet_table(seed, num_packets) if lengths is None else \
+        synth.packet_table(seed, num_packets, lengths=tuple(lengths))
+    layout = []
+    tin = tout = tsyn = tdat = 0
+    for sp in specs:
+        m, k = code_params(sp.n)
+        iw, ow, dw = hd.words_for(sp.num_codewords * sp.n), hd.words_for(sp.num_codewords * k), \
+            hd.words_for(sp.num_codewords * k)
+        layout.append((sp.n, sp.num_codewords, tin, tout, tsyn, tdat, iw, ow, dw))
+        tin += align4(iw)
+        tout += align4(ow)
+        tsyn += (sp.num_codewords + 15) // 16 * 16
+        tdat += align4(dw)
+    data_h = np.zeros(tdat, np.uint32)
+    for j, (n, N, oi, oo, osy, od, iw, ow, dw) in enumerate(layout):
+        m, k = code_params(n)
+        data_h[od:od + dw] = synth.random_words(seed * 100003 + j, N * k)
+    d_data = torch.from_numpy(data_h.view(np.int32)).to(dev)
+    d_in = torch.zeros(tin, dtype=torch.int32, device=dev)
+    base_in, base_data = d_in.data_ptr(), d_data.data_ptr()
+    sh = torch.cuda.current_stream(dev).cuda_stream
+    for (n, N, oi, oo, osy, od, iw, ow, dw) in layout:
+        hd.check(hd.hd_encode(base_data + 4 * od, n, N, base_in + 4 * oi, sh), "hd_encode")
+    # channel errors: flip bits on the device, one XOR per touched word
+    words, masks = [], []
+    for j, (n, N, oi, oo, osy, od, iw, ow, dw) in enumerate(layout):
+        b = synth.error_events(seed * 100003 + j, n, N, p1=BATCH_P1).stream_bits()
+        words.append(oi + (b >> 5))
+        masks.append((np.uint32(1) << (b & 31).astype(np.uint32)))
+    wv = np.concatenate(words)
+    mv = np.concatenate(masks)
+    order = np.argsort(wv, kind="stable")
+    wv, mv = wv[order], mv[order]
+    uniq, start = np.unique(wv, return_index=True)
+    mx = np.bitwise_xor.reduceat(mv, start) if wv.size else mv
+    idx = torch.from_numpy(uniq.astype(np.int64)).to(dev)
+    msk = torch.from_numpy(mx.view(np.int32)).to(dev)
+    d_in[idx] = torch.bitwise_xor(d_in[idx], msk)
+    del d_data
+    d_out = torch.empty(max(1, tout), dtype=torch.int32, device=dev)
+    d_syn = torch.empty(max(16, tsyn), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    return layout, d_in, d_out, d_syn
+
+
+def run_batched(dev, args, peak):
+    import torch
+    from paper_1412_6862_gb300 import hd
+    t_setup = time.perf_counter()
+    layout, d_in, d_out, d_syn = build_batched(dev, args.batched_packets)
+    P = len(layout)
+    bi, bo, bs = d_in.data_ptr(), d_out.data_ptr(), d_syn.data_ptr()
+    rows = [(bi + 4 * oi, bo + 4 * oo, bs + osy, N, n, hd.SYN_U8) for (n, N, oi, oo, osy, od, iw, ow, dw) in layout]
+    table = hd.packet_table(rows)
+    err = torch.empty(P, dtype=torch.int64, device=dev)
+    bits = sum(N * code_params(n)[1] for (n, N, *_r) in layout)
+    nbytes = sum((N * n + 7) // 8 + (N * code_params(n)[1] + 7) // 8 + N for (n, N, *_r) in layout)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    plan = hd.hd_plan_create(table, P)
+    tuned = hd.hd_plan_autotune(plan, 2, stream)
+    setup_s = time.perf_counter() - t_setup
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / 1e3 / reps
+
+    def persistent():
+        hd.check(hd.hd_plan_launch(plan, err.data_ptr(), sh), "hd_plan_launch")
+
+    t_pers = timed(persistent, args.batched_steps)
+
+    def per_packet(cuda_stream):
+        for (a, b, c, N, n, st) in rows:
+            rc = hd.hd_decode(a, N * n, n, N, b, c, st, None, cuda_stream)
+            if rc != 0:
+                raise hd.HDError(rc, "hd_decode")
+
+    t_eager = timed(lambda: per_packet(sh), 2)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        per_packet(torch.cuda.current_stream(dev).cuda_stream)
+    t_graph = timed(g.replay, 3)
+    del g
+    hd.hd_plan_destroy(plan)
+    gbps = lambda t: bits / t / 1e9
+    return {
+        "workload": f"batched mixed-n: {P} packets, n uniform over {{7,15,31,63,127,255}}, length log-uniform "
+                    f"64 bit..4 Mbit rounded to whole codewords, p1={BATCH_P1}, u8 syndromes + per-packet err_count",
+        "packets": P, "codewords": int(sum(N for (n, N, *_r) in layout)), "decoded_bits": int(bits),
+        "algorithmic_bytes": int(nbytes),
+        "persistent_graph": {"gbps": gbps(t_pers), "ms": t_pers * 1e3, "hbm_frac": nbytes / t_pers / 1e9 / peak,
+                             "warps_per_cta": tuned["warps_per_cta"], "stages": tuned["stages"],
+                             "tiles": tuned["num_tiles"]},
+        "per_packet_eager": {"gbps": gbps(t_eager), "ms": t_eager * 1e3},
+        "per_packet_graph": {"gbps": gbps(t_graph), "ms": t_graph * 1e3},
+        "speedup_vs_per_packet_eager": t_eager / t_pers,
+        "speedup_vs_per_packet_graph": t_graph / t_pers,
+        "setup_s": setup_s,
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -240,6 +370,12 @@ def run_ours(args):
     from paper_1412_6862_gb300 import build as hd_build
     hd_build.build()
     from paper_1412_6862_gb300 import hd, synth
+
+    if args.batched_only:
+        res = run_batched(dev, args, peaks()[0])
+        if rank == 0:
+            print(json.dumps({"batched": res}), flush=True)
+        return
 
     codes = tuple(int(c) for c in args.codes.split(","))
     assert all(c in SWEEP_CODES for c in codes), codes
@@ -370,6 +506,14 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = bits_per_step * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
 
+    batched = None
+    if not args.no_batched:
+        for b in bufs.values():  # free the sweep's buffers first
+            b.clear()
+        bufs.clear()
+        torch.cuda.empty_cache()
+        batched = run_batched(dev, args, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -391,6 +535,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -201,11 +201,11 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
  * that budgets all device memory up front, an application whose allocator
  * hooks forbid allocations from inside libraries, or a latency-critical
  * receive path where an allocation could stall or fail.  It decodes exactly
- * like hd_decode_batch(), but its packet table, tile table and claim counter
- * live in one fixed 1 MiB array compiled into libhd.so; every device that
+ * like hd_decode_batch(), but its tile table (one 64-byte descriptor per
+ * tile) and claim counter live in one fixed 1 MiB array compiled into libhd.so; every device that
  * loads the library holds that array until the process exits.
  *
- * Limits: at most 4096 packets and 49,136 tiles (a tile is a chunk of 256 to
+ * Limits: at most 4096 packets and 16,380 tiles (a tile is one to four chunks of 256 to
  * 1024 codewords, or up to 1024 codewords of a packet's tail); larger batches
  * return HD_ERR_CAPACITY before anything is enqueued.
  * First call on a device: performs a one-time set-up (it looks up the array's

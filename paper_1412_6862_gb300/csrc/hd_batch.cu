@@ -9,9 +9,10 @@
 // tiles grouped by n, then the tails), prefetch S claimed tiles ahead into
 // their own shared-memory stages with 1-D bulk copies, decode full tiles with
 // the same per-warp chunk decoder as the streaming kernel, decode tails with
-// the generic warp-tile decoder straight from global memory, and add each
-// tile's nonzero-syndrome count to its packet's error counter.  Dynamic
-// claiming balances packets whose lengths span six orders of magnitude.
+// the chunk decoder too (copied in, zero-padded to a chunk, copied back out;
+// n = 3 tails use the generic warp-tile decoder), and add each tile's
+// nonzero-syndrome count to its packet's error counter.  Dynamic claiming of
+// bounded tiles balances packets whose lengths span six orders of magnitude.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -37,48 +38,96 @@ struct DevPacket {
     uint32_t pad;
 };
 
+// A self-contained work item: everything a warp needs to decode it, so that
+// the warp never chases a second table.
 struct DevTile {
-    uint32_t packet;
-    uint32_t count;  // codewords, | kFullTile for a whole chunk of 32*G decoded by the chunk decoder
-    uint64_t c0;     // first codeword (a multiple of 32)
+    const uint32_t *in;  // packet input (word 0 = codeword 0)
+    uint32_t *out;       // packet output
+    uint8_t *syn;        // packet syndromes (NULL when syn_type is 0)
+    uint64_t num_cw;     // packet length in codewords
+    uint64_t c0;         // first codeword of the tile (a multiple of 32)
+    uint32_t packet;     // index into err_counts
+    uint32_t count;      // codewords, | kFullTile for whole chunks of 32*G decoded by the chunk decoder
+    uint32_t bytes;      // bulk-load size of a full tile (0 for a tail)
+    uint16_t n;
+    uint8_t m;
+    uint8_t syn_type;
+    uint64_t pad;
 };
 
 constexpr uint32_t kFullTile = 0x80000000u;
 
-// Generic (tail) tiles are cut to at most this many codewords.
+inline DevTile make_tile(const uint32_t *in, uint32_t *out, uint8_t *syn, uint64_t num_cw, uint32_t n, uint32_t m,
+                         uint32_t syn_type, uint32_t packet, uint64_t c0, uint32_t count, uint32_t bytes)
+{
+    DevTile t;
+    t.in = in;
+    t.out = out;
+    t.syn = syn;
+    t.num_cw = num_cw;
+    t.c0 = c0;
+    t.packet = packet;
+    t.count = count;
+    t.bytes = bytes;
+    t.n = (uint16_t)n;
+    t.m = (uint8_t)m;
+    t.syn_type = (uint8_t)syn_type;
+    t.pad = 0;
+    return t;
+}
+
+// Tails are cut to at most this many codewords (a tail of n >= 7 is shorter
+// than one chunk anyway; n = 3 streams are all tail).
 constexpr uint64_t kTailTile = 1024;
 
 __host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 255 ? 8 : (n >= 127 ? 16 : 32); }
 
-constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest chunk input (n=255, G=8: 8160 B) + spare
-constexpr uint32_t kBatchSynBytes = 32 * 32 * 2;  // largest chunk syndromes (G=32, u16)
+// Chunks per full tile: small codes pack several chunks (at most 4096
+// codewords) so that every tile moves several KB and the per-tile overhead
+// and load latency are amortised.
+__host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 15 ? 4 : (n <= 31 ? 2 : 1); }
+
+constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest tile input (n=255: 8160 B; n=31: 7936 B) + spare
+constexpr uint32_t kBatchSynBytes = 4 * 32 * 32 * 2;  // largest tile syndromes (4 chunks of 1024, u16)
 
 template <int WARPS, int S>
 struct BatchCfg {
     static constexpr uint32_t off_bar = 0;
-    static constexpr uint32_t off_claim = 64;
-    static constexpr uint32_t off_stage = 128;
+    static constexpr uint32_t off_claim = 64;  // per stage: the claimed tile index and its descriptor
+    static constexpr uint32_t off_desc = 128;
+    static constexpr uint32_t off_stage = off_desc + 8 * 64;
     static constexpr uint32_t off_syn = off_stage + S * kBatchStageBytes;
-    static constexpr uint32_t warp_bytes = (off_syn + 2 * kBatchSynBytes + 127) / 128 * 128;
+    // one syndrome buffer: every store has read its sources before the next tile starts
+    static constexpr uint32_t warp_bytes = (off_syn + kBatchSynBytes + 127) / 128 * 128;
     static constexpr uint32_t smem = WARPS * warp_bytes;
-    static_assert(S >= 2 && S <= 8, "stages");
+    static_assert(S >= 1 && S <= 8, "stages");
     static_assert(kWarpSlotWords * 4 * 2 <= kBatchStageBytes, "generic slots fit a stage");
     static_assert(smem <= 232448, "shared memory per CTA");
 };
 
+// Decode the `chunks` whole chunks of a full tile held in `stage`, in place:
+// chunk c's output goes to stage + c*out_words, which never overlaps a later
+// chunk's input because k < n.
 template <int N_, int SYN>
-__device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sbuf, int lane)
+__device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sbuf, int lane, uint32_t chunks)
 {
-    return decode_warp_chunk<N_, SYN, batch_G(N_)>(stage, const_cast<uint32_t *>(stage), sbuf, lane);
+    using Q = ChunkGeom<N_, SYN, batch_G(N_)>;
+    uint32_t e = 0;
+    for (uint32_t c = 0; c < chunks; ++c)
+        e += decode_warp_chunk<N_, SYN, batch_G(N_)>(stage + c * Q::in_words,
+                                                      const_cast<uint32_t *>(stage) + c * Q::out_words,
+                                                      sbuf + c * Q::syn_bytes, lane);
+    return e;
 }
 
 template <int N_>
-__device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sbuf, int lane)
+__device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sbuf, int lane,
+                                                    uint32_t chunks)
 {
     switch (syn_type) {
-        case 1: return batch_chunk<N_, 1>(stage, sbuf, lane);
-        case 2: return batch_chunk<N_, 2>(stage, sbuf, lane);
-        default: return batch_chunk<N_, 0>(stage, sbuf, lane);
+        case 1: return batch_chunk<N_, 1>(stage, sbuf, lane, chunks);
+        case 2: return batch_chunk<N_, 2>(stage, sbuf, lane, chunks);
+        default: return batch_chunk<N_, 0>(stage, sbuf, lane, chunks);
     }
 }
 
@@ -86,9 +135,8 @@ __device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return 32u * (
 
 template <int WARPS, int S>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_decode_batch(const DevPacket *__restrict__ pk, const DevTile *__restrict__ tiles, uint32_t num_tiles,
-                   uint32_t *__restrict__ counter, unsigned long long *__restrict__ err_counts,
-                   uint32_t *__restrict__ status)
+    k_decode_batch(const DevTile *__restrict__ tiles, uint32_t num_tiles, uint32_t *__restrict__ counter,
+                   unsigned long long *__restrict__ err_counts, uint32_t *__restrict__ status)
 {
     using Cfg = BatchCfg<WARPS, S>;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -96,32 +144,38 @@ __global__ void __launch_bounds__(WARPS * 32)
     uint8_t *wbase = smem + warp * Cfg::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
     volatile uint32_t *claim = reinterpret_cast<volatile uint32_t *>(wbase + Cfg::off_claim);
+    DevTile *desc = reinterpret_cast<DevTile *>(wbase + Cfg::off_desc);
     uint8_t *s_stage = wbase + Cfg::off_stage;
     uint8_t *s_syn = wbase + Cfg::off_syn;
 
-    // lane 0: claim the next tile into stage s and start its load (tails load nothing)
-    auto issue = [&](int s) {
-        const uint32_t t = atomicAdd(counter, 1u);
+    // lane 0: record claim t with descriptor d in stage s's slot and start its
+    // load (tails are read by the whole warp later; past-the-end claims load nothing)
+    auto issue = [&](int s, uint32_t t, const DevTile &d) {
         claim[s] = t;
-        bool loading = false;
-        if (t < num_tiles) {
-            const DevTile tl = tiles[t];
-            const DevPacket &p = pk[tl.packet];
-            if (tl.count & kFullTile) {
-                const uint32_t bytes = chunk_codewords(p.n) * p.n / 8u;
-                mbar_arrive_expect_tx(&bar[s], bytes);
-                bulk_g2s(s_stage + s * kBatchStageBytes, p.in + tl.c0 * p.n / 32u, bytes, &bar[s]);
-                loading = true;
-            }
+        if (t < num_tiles) desc[s] = d;
+        if (t < num_tiles && d.bytes != 0) {
+            mbar_arrive_expect_tx(&bar[s], d.bytes);
+            bulk_g2s(s_stage + s * kBatchStageBytes, d.in + d.c0 * d.n / 32u, d.bytes, &bar[s]);
+        } else {
+            mbar_arrive(&bar[s]);
         }
-        if (!loading) mbar_arrive(&bar[s]);
     };
-
+    // Claims run one iteration ahead of their use: the atomic issued while a
+    // tile is decoded returns long before its result is needed, and the
+    // claimed tile's descriptor is fetched during the next decode.
+    uint32_t next_t = 0;
+    DevTile next_d{};
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
-        for (int s = 0; s < S; ++s) issue(s);
+        for (int s = 0; s < S; ++s) {
+            const uint32_t t = atomicAdd(counter, 1u);
+            DevTile d{};
+            if (t < num_tiles) d = tiles[t];
+            issue(s, t, d);
+        }
+        next_t = atomicAdd(counter, 1u);
     }
     __syncwarp();
 
@@ -136,40 +190,83 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         const uint32_t t = claim[s];
         if (t >= num_tiles) break;  // claims only grow: every later stage is past the end too
-        const DevTile tl = tiles[t];
-        const DevPacket p = pk[tl.packet];
+        // every iteration refills its stage at its end: fetch the descriptor of
+        // the tile claimed last iteration and claim the next one
+        uint32_t later_t = 0;
+        if (lane == 0) {
+            if (next_t < num_tiles) next_d = tiles[next_t];  // used at the end of this iteration
+            later_t = atomicAdd(counter, 1u);                // used at the end of the next one
+        }
+        const DevTile tl = desc[s];  // written by lane 0 before the stage's arrive
+        struct {
+            const uint32_t *in;
+            uint32_t *out;
+            uint8_t *syn;
+            uint64_t num_cw, in_words, out_words;
+            uint32_t n, m, syn_type;
+        } p{tl.in, tl.out, tl.syn, tl.num_cw, (tl.num_cw * tl.n + 31) / 32, (tl.num_cw * (tl.n - tl.m) + 31) / 32,
+            tl.n, tl.m, tl.syn_type};
         const bool full = (tl.count & kFullTile) != 0;
+        const uint32_t chunks = full ? (tl.count & ~kFullTile) / chunk_codewords(p.n) : 0u;
         uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * kBatchStageBytes);
-        uint8_t *sbuf = s_syn + (it & 1u) * kBatchSynBytes;
+        uint8_t *sbuf = s_syn;
         unsigned long long errs = 0;
-        if (full) {
+        if (full || p.n != 3) {
+            const uint32_t cwords = chunk_codewords(p.n);
+            const uint32_t k = p.n - p.m;
+            const uint32_t cnt = tl.count & ~kFullTile;
+            if (!full) {
+                // ragged tail of cnt < one chunk: copy it in with coalesced loads,
+                // drop the input pad bits and zero-fill the chunk, so that the
+                // padding decodes to zero data bits and zero syndromes
+                const uint32_t iw = (cnt * p.n + 31) / 32, cw_words = cwords * p.n / 32 + 4;
+                const uint32_t tail_bits = (cnt * p.n) & 31u;
+                const uint32_t *src = p.in + tl.c0 * p.n / 32u;
+                for (uint32_t w = lane; w < cw_words; w += 32) {
+                    uint32_t v = w < iw ? src[w] : 0u;
+                    if (w == iw - 1 && tail_bits != 0) v &= (1u << tail_bits) - 1u;
+                    stage[w] = v;
+                }
+                __syncwarp();
+            }
             uint32_t e = 0;
+            const uint32_t nch = full ? chunks : 1u;
             switch (p.n) {
-                case 7: e = batch_chunk_syn<7>(p.syn_type, stage, sbuf, lane); break;
-                case 15: e = batch_chunk_syn<15>(p.syn_type, stage, sbuf, lane); break;
-                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sbuf, lane); break;
-                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sbuf, lane); break;
-                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sbuf, lane); break;
-                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sbuf, lane); break;
-                default: break;  // the plan never makes full tiles of other lengths
+                case 7: e = batch_chunk_syn<7>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 15: e = batch_chunk_syn<15>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sbuf, lane, nch); break;
+                default: break;  // the plan never makes chunk tiles of other lengths
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
             errs = e;
+            if (!full) {
+                // write back only the tail's words and syndromes
+                __syncwarp();
+                const uint32_t ow = (cnt * k + 31) / 32;
+                uint32_t *dst = p.out + tl.c0 * k / 32u;
+                for (uint32_t w = lane; w < ow; w += 32) dst[w] = stage[w];
+                if (p.syn_type == 1)
+                    for (uint32_t i = lane; i < cnt; i += 32) p.syn[tl.c0 + i] = sbuf[i];
+                else if (p.syn_type == 2)
+                    for (uint32_t i = lane; i < cnt; i += 32)
+                        reinterpret_cast<uint16_t *>(p.syn)[tl.c0 + i] = reinterpret_cast<const uint16_t *>(sbuf)[i];
+            }
             fence_proxy_async_smem();
             __syncwarp();
         } else {
-            // ragged tail: generic warp tiles, the (unloaded) stage as slot memory
+            // n = 3: generic warp tiles, the (unloaded) stage as slot memory
             errs = generic_decode_tiles(p.in, p.in_words, p.n, p.m, p.num_cw, tl.c0 / 32, (tl.c0 + tl.count + 31) / 32,
                                         1, p.out, p.out_words, p.syn, (int)p.syn_type, stage, stage + kWarpSlotWords);
+            fence_proxy_async_smem();
             __syncwarp();
         }
         if (lane == 0) {
-            // the store issued last iteration has finished reading its stage: refill that stage
-            bulk_wait_read<0>();
-            if (it > 0) issue((int)((it - 1) % S));
             if (full) {
-                const uint32_t cw = chunk_codewords(p.n);
+                const uint32_t cw = tl.count & ~kFullTile;
                 const uint32_t k = p.n - p.m;
                 bulk_s2g(p.out + tl.c0 * k / 32u, stage, cw * k / 8u);
                 if (p.syn_type != 0) {
@@ -178,6 +275,11 @@ __global__ void __launch_bounds__(WARPS * 32)
                 }
                 bulk_commit();
             }
+            // the stage holds this tile's output: once the store has read it,
+            // refill the stage with the tile claimed last iteration
+            bulk_wait_read<0>();
+            issue(s, next_t, next_d);
+            next_t = later_t;
             if (err_counts != nullptr && errs != 0) atomicAdd(&err_counts[tl.packet], errs);
         }
         __syncwarp();
@@ -185,7 +287,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (lane == 0) {
         if (aborted) {
             atomicOr(status, (uint32_t)HD_ERR_TIMEOUT);
-            for (uint32_t j = it; j < it + S - 1; ++j) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+            for (uint32_t j = it; j < it + S; ++j) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
         }
         bulk_wait_all<0>();
     }
@@ -198,15 +300,15 @@ struct BatchVariant {
     int warps, stages;
     uint32_t smem;
     const void *kernel;
-    void (*launch)(int grid, uint32_t smem, cudaStream_t st, const DevPacket *, const DevTile *, uint32_t, uint32_t *,
+    void (*launch)(int grid, uint32_t smem, cudaStream_t st, const DevTile *, uint32_t, uint32_t *,
                    unsigned long long *, uint32_t *);
 };
 
 template <int W, int S>
-void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevPacket *pk, const DevTile *tiles,
-                         uint32_t num_tiles, uint32_t *counter, unsigned long long *err, uint32_t *status)
+void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevTile *tiles, uint32_t num_tiles,
+                         uint32_t *counter, unsigned long long *err, uint32_t *status)
 {
-    k_decode_batch<W, S><<<grid, W * 32, smem, st>>>(pk, tiles, num_tiles, counter, err, status);
+    k_decode_batch<W, S><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status);
 }
 
 template <int W, int S>
@@ -223,8 +325,8 @@ BatchVariant make_batch_variant()
 
 static const std::vector<BatchVariant> &batch_variants()
 {
-    static const std::vector<BatchVariant> v = {make_batch_variant<2, 2>(), make_batch_variant<4, 2>(),
-                                                make_batch_variant<2, 3>()};
+    static const std::vector<BatchVariant> v = {make_batch_variant<2, 2>(), make_batch_variant<1, 3>(),
+                                                make_batch_variant<2, 3>(), make_batch_variant<1, 4>()};
     return v;
 }
 
@@ -240,7 +342,6 @@ struct hd_plan {
     uint64_t codewords = 0;
     uint64_t in_bytes = 0, out_bytes = 0, syn_bytes = 0;
     void *dmem = nullptr;
-    DevPacket *d_pk = nullptr;
     DevTile *d_tiles = nullptr;
     uint32_t *d_counter = nullptr;
     int variant = 0;
@@ -288,7 +389,8 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
         d.pad = 0;
         const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
         const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
-        ntiles += nfull + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+        const uint64_t per = (uint64_t)batch_chunks(q.n);
+        ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
         if (stats) {
             stats->codewords += q.num_codewords;
             stats->in_bytes += (q.num_codewords * q.n + 7) / 8;
@@ -308,9 +410,15 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
             const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
             // n = 3 has no chunk decoder: all its codewords take the generic path
             const uint64_t nfull = n == 3 ? 0 : d.num_cw / chunk;
-            for (uint64_t j = 0; j < nfull; ++j) tiles.push_back(DevTile{i, (uint32_t)chunk | kFullTile, j * chunk});
+            const uint64_t per = (uint64_t)batch_chunks(n);
+            for (uint64_t j = 0; j < nfull; j += per) {
+                const uint64_t c = std::min(per, nfull - j);
+                tiles.push_back(make_tile(d.in, d.out, d.syn, d.num_cw, n, d.m, d.syn_type, i, j * chunk,
+                                          (uint32_t)(c * chunk) | kFullTile, (uint32_t)(c * chunk * n / 8)));
+            }
             for (uint64_t c = nfull * chunk; c < d.num_cw; c += kTailTile)
-                tails.push_back(DevTile{i, (uint32_t)std::min<uint64_t>(kTailTile, d.num_cw - c), c});
+                tails.push_back(make_tile(d.in, d.out, d.syn, d.num_cw, n, d.m, d.syn_type, i, c,
+                                          (uint32_t)std::min<uint64_t>(kTailTile, d.num_cw - c), 0u));
         }
     }
     if (stats) stats->full_tiles = (uint32_t)tiles.size();
@@ -354,7 +462,7 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
         if (e != cudaSuccess) return e;
     }
     if (p->num_tiles == 0) return cudaSuccess;
-    v.launch(grid, v.smem, st, p->d_pk, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status);
+    v.launch(grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status);
     return cudaGetLastError();
 }
 
@@ -387,18 +495,14 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     cudaGetDevice(&p->device);
     p->num_packets = num_packets;
     p->num_tiles = (uint32_t)tiles.size();
-    const size_t pk_b = (pk.size() * sizeof(DevPacket) + 255) / 256 * 256;
     const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
-    if (cudaMalloc(&p->dmem, pk_b + tl_b + 256) != cudaSuccess) {
+    if (cudaMalloc(&p->dmem, tl_b + 256) != cudaSuccess) {
         delete p;
         return HD_ERR_CUDA;
     }
-    p->d_pk = static_cast<DevPacket *>(p->dmem);
-    p->d_tiles = reinterpret_cast<DevTile *>(static_cast<char *>(p->dmem) + pk_b);
-    p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + pk_b + tl_b);
-    if ((!pk.empty() && cudaMemcpy(p->d_pk, pk.data(), pk.size() * sizeof(DevPacket), cudaMemcpyHostToDevice) !=
-                            cudaSuccess) ||
-        (!tiles.empty() &&
+    p->d_tiles = static_cast<DevTile *>(p->dmem);
+    p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + tl_b);
+    if ((!tiles.empty() &&
          cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) != cudaSuccess) {
         cudaFree(p->dmem);
@@ -532,18 +636,14 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
     if (rc != HD_OK) return rc;
     p.num_packets = num_packets;
     p.num_tiles = (uint32_t)tiles.size();
-    const size_t pk_b = (pk.size() * sizeof(DevPacket) + 255) / 256 * 256;
     const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
     // stream-ordered scratch: freed on the stream once the kernel has run
-    if (cudaMallocAsync(&p.dmem, pk_b + tl_b + 256, st) != cudaSuccess) return HD_ERR_CUDA;
-    p.d_pk = static_cast<DevPacket *>(p.dmem);
-    p.d_tiles = reinterpret_cast<DevTile *>(static_cast<char *>(p.dmem) + pk_b);
-    p.d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p.dmem) + pk_b + tl_b);
-    // pageable sources: the copies have read the host vectors when these calls return
-    if ((!pk.empty() && cudaMemcpyAsync(p.d_pk, pk.data(), pk.size() * sizeof(DevPacket), cudaMemcpyHostToDevice,
-                                        st) != cudaSuccess) ||
-        (!tiles.empty() && cudaMemcpyAsync(p.d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
-                                           cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+    if (cudaMallocAsync(&p.dmem, tl_b + 256, st) != cudaSuccess) return HD_ERR_CUDA;
+    p.d_tiles = static_cast<DevTile *>(p.dmem);
+    p.d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p.dmem) + tl_b);
+    // pageable source: the copy has read the host vector when this call returns
+    if (!tiles.empty() && cudaMemcpyAsync(p.d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
+                                          cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaFreeAsync(p.dmem, st);
         return HD_ERR_CUDA;
     }
@@ -564,8 +664,8 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
 // For callers that must not allocate device memory -- a process that budgets
 // every byte of device memory up front, an application whose allocator hooks
 // forbid allocations from inside libraries, or a latency-critical receive
-// path where an allocation could stall or fail -- the packet table, the tile
-// table and the claim counter of the batched decoder live in one fixed array
+// path where an allocation could stall or fail -- the tile table and the
+// claim counter of the batched decoder live in one fixed array
 // compiled into this library.  The array is kNoAllocBytes (1 MiB) on every
 // device that loads the library and stays there until the process exits.
 // ---------------------------------------------------------------------------
@@ -574,18 +674,17 @@ namespace {
 
 constexpr uint32_t kNoAllocBytes = 1u << 20;
 constexpr uint32_t kNoAllocMaxPackets = 4096;
-constexpr uint32_t kNoAllocPacketsOff = 256;  // the claim counter sits at offset 0
-constexpr uint32_t kNoAllocTilesOff = kNoAllocPacketsOff + kNoAllocMaxPackets * sizeof(DevPacket);
+constexpr uint32_t kNoAllocTilesOff = 256;  // the claim counter sits at offset 0
 constexpr uint32_t kNoAllocMaxTiles = (kNoAllocBytes - kNoAllocTilesOff) / sizeof(DevTile);
-static_assert(sizeof(DevPacket) == 64 && sizeof(DevTile) == 16, "table layout");
+static_assert(sizeof(DevTile) == 64, "table layout");
 
 // The device scratch.  In host code this name is only a handle for
 // cudaGetSymbolAddress; kernels receive the device address it returns.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Host image of the tables, uploaded with one copy per table.  The copies read
-// pageable memory, so they have consumed it when cudaMemcpyAsync returns and
-// the next call may rewrite it; the mutex serialises host threads.
+// Host image of the tile table, uploaded with one copy.  The copy reads
+// pageable memory, so it has consumed it when cudaMemcpyAsync returns and the
+// next call may rewrite it; the mutex serialises host threads.
 alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
 std::mutex g_noalloc_mu;
 constexpr int kNoAllocMaxDevices = 64;
@@ -635,7 +734,8 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
         }
         const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
         const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
-        ntiles += nfull + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+        const uint64_t per = (uint64_t)batch_chunks(q.n);
+        ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
     }
     if (ntiles > kNoAllocMaxTiles) return HD_ERR_CAPACITY;
     const hd_status su = noalloc_setup(dev);
@@ -643,40 +743,32 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
     unsigned char *dbase = g_noalloc_dev[dev];
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // host image: packets, then full tiles grouped by n (long codes first), then tails
-    DevPacket *hp = reinterpret_cast<DevPacket *>(g_noalloc_host + kNoAllocPacketsOff);
+    // host image: full tiles grouped by n (long codes first), then tails
     DevTile *ht = reinterpret_cast<DevTile *>(g_noalloc_host + kNoAllocTilesOff);
-    for (uint32_t i = 0; i < num_packets; ++i) {
-        const hd_packet &q = table[i];
-        const uint32_t m = (uint32_t)code_m(q.n);
-        DevPacket &d = hp[i];
-        d.in = q.in;
-        d.out = q.out;
-        d.syn = static_cast<uint8_t *>(q.syndromes);
-        d.num_cw = q.num_codewords;
-        d.n = q.n;
-        d.m = m;
-        d.syn_type = q.syndromes ? q.syn_type : 0;
-        d.in_words = words_for_bits(q.num_codewords * q.n);
-        d.out_words = words_for_bits(q.num_codewords * (q.n - m));
-        d.pad = 0;
-    }
     uint32_t t = 0;
     static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
-    for (uint32_t n : order)
-        for (uint32_t i = 0; i < num_packets; ++i) {
-            if (hp[i].n != n || n == 3) continue;
-            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
-            for (uint64_t j = 0; j < hp[i].num_cw / chunk; ++j) ht[t++] = DevTile{i, (uint32_t)chunk | kFullTile, j * chunk};
-        }
-    for (uint32_t n : order)
-        for (uint32_t i = 0; i < num_packets; ++i) {
-            if (hp[i].n != n) continue;
-            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
-            const uint64_t first = n == 3 ? 0 : hp[i].num_cw / chunk * chunk;
-            for (uint64_t c = first; c < hp[i].num_cw; c += kTailTile)
-                ht[t++] = DevTile{i, (uint32_t)std::min<uint64_t>(kTailTile, hp[i].num_cw - c), c};
-        }
+    for (int pass = 0; pass < 2; ++pass)
+        for (uint32_t n : order)
+            for (uint32_t i = 0; i < num_packets; ++i) {
+                const hd_packet &q = table[i];
+                if (q.n != n) continue;
+                const uint32_t m = (uint32_t)code_m(n);
+                const uint32_t st_i = q.syndromes ? q.syn_type : 0u;
+                uint8_t *sy = static_cast<uint8_t *>(q.syndromes);
+                const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+                const uint64_t nfull = n == 3 ? 0 : q.num_codewords / chunk, per = (uint64_t)batch_chunks(n);
+                if (pass == 0) {
+                    for (uint64_t j = 0; j < nfull; j += per) {
+                        const uint64_t c = std::min(per, nfull - j);
+                        ht[t++] = make_tile(q.in, q.out, sy, q.num_codewords, n, m, st_i, i, j * chunk,
+                                            (uint32_t)(c * chunk) | kFullTile, (uint32_t)(c * chunk * n / 8));
+                    }
+                } else {
+                    for (uint64_t c = nfull * chunk; c < q.num_codewords; c += kTailTile)
+                        ht[t++] = make_tile(q.in, q.out, sy, q.num_codewords, n, m, st_i, i, c,
+                                            (uint32_t)std::min<uint64_t>(kTailTile, q.num_codewords - c), 0u);
+                }
+            }
 
     // the claim counter must start at zero; the error counters are overwritten
     uint32_t *counter = reinterpret_cast<uint32_t *>(dbase);
@@ -685,15 +777,12 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
         cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * num_packets, st) != cudaSuccess)
         return HD_ERR_CUDA;
     if (t == 0) return HD_OK;
-    if (cudaMemcpyAsync(dbase + kNoAllocPacketsOff, hp, sizeof(DevPacket) * num_packets, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(dbase + kNoAllocTilesOff, ht, sizeof(DevTile) * t, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMemcpyAsync(dbase + kNoAllocTilesOff, ht, sizeof(DevTile) * t, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return HD_ERR_CUDA;
     const BatchVariant &v = batch_variants()[0];
     const int grid = batch_grid(v, t);
     if (grid <= 0) return HD_ERR_CUDA;
-    v.launch(grid, v.smem, st, reinterpret_cast<const DevPacket *>(dbase + kNoAllocPacketsOff),
-             reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
+    v.launch(grid, v.smem, st, reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
              g_noalloc_status[dev]);
     if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
     count_launch();

@@ -10,8 +10,9 @@
 //
 // INPLACE: the decoded words overwrite the chunk's own input stage (the warp
 // first copies the chunk to registers), which removes the output staging
-// buffers so that more warps fit on an SM; the stage is refilled once its bulk
-// store has finished reading it.
+// buffers so that more warps fit on an SM; a stage is refilled one iteration
+// later, once its bulk store has finished reading it (waiting for that read
+// right after issuing the store costs more than the lost lookahead).
 #pragma once
 
 #include <cstdint>
@@ -174,7 +175,8 @@ __global__ void __launch_bounds__(T)
         __syncwarp();
         if (lane == 0) {
             if constexpr (INPLACE) {
-                // the store issued last iteration has finished reading its stage: refill that stage
+                // the store issued last iteration has finished reading its stage: refill that
+                // stage with the chunk S iterations after it (so in place the lookahead is S - 1)
                 bulk_wait_read<0>();
                 if (it > 0) {
                     const uint64_t cn = c - tw + (uint64_t)S * tw;

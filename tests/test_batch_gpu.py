@@ -110,3 +110,57 @@ def test_plan_autotune_and_long_packets():
     torch.cuda.synchronize()
     check_batch(pkts, exp, err)
     plan.close()
+
+
+def test_batched_config_full_size():
+    """The batched benchmark configuration at full size (10,000 packets, n
+    uniform over six codes, log-uniform lengths up to 4 Mbit), every packet
+    compared with the oracle.  Inputs: oracle encoder + generator errors."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    specs = synth.packet_table(0, 10000)
+
+    def make(j):
+        sp = specs[j]
+        m, k = hd.code_params(sp.n)
+        data = synth.random_words(j, sp.num_codewords * k)
+        s = oracle.encode(data, sp.n, sp.num_codewords)
+        synth.apply_errors(s, synth.error_events(j, sp.n, sp.num_codewords, p1=0.05))
+        return s, oracle.decode(s, sp.n, sp.num_codewords, syn_type=oracle.SYN_U8)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        made = list(ex.map(make, range(len(specs))))
+    # arenas with 16-byte aligned packets
+    offs_in, offs_out, offs_syn, tin, tout, tsyn = [], [], [], 0, 0, 0
+    for sp, (s, _) in zip(specs, made):
+        m, k = hd.code_params(sp.n)
+        offs_in.append(tin)
+        offs_out.append(tout)
+        offs_syn.append(tsyn)
+        tin += (s.size + 3) // 4 * 4
+        tout += (hd.words_for(sp.num_codewords * k) + 3) // 4 * 4
+        tsyn += (sp.num_codewords + 15) // 16 * 16
+    h_in = np.zeros(tin, np.uint32)
+    for o, (s, _) in zip(offs_in, made):
+        h_in[o:o + s.size] = s
+    d_in = torch.from_numpy(h_in.view(np.int32)).cuda()
+    d_out = torch.full((tout,), -1, dtype=torch.int32, device="cuda")
+    d_syn = torch.full((tsyn,), 0xEE, dtype=torch.uint8, device="cuda")
+    rows = [(d_in.data_ptr() + 4 * oi, d_out.data_ptr() + 4 * oo, d_syn.data_ptr() + osy, sp.num_codewords, sp.n,
+             hd.SYN_U8) for sp, oi, oo, osy in zip(specs, offs_in, offs_out, offs_syn)]
+    table = hd.packet_table(rows)
+    plan = hd.hd_plan_create(table, len(rows))
+    err = torch.empty(len(rows), dtype=torch.int64, device="cuda")
+    assert hd.hd_plan_launch(plan, err.data_ptr(), torch.cuda.current_stream().cuda_stream) == hd.HD_OK
+    torch.cuda.synchronize()
+    hd.hd_plan_destroy(plan)
+    o_h = d_out.cpu().numpy().view(np.uint32)
+    s_h = d_syn.cpu().numpy()
+    e_h = err.cpu().numpy()
+    for j, (sp, (s, (eo, es, ee))) in enumerate(zip(specs, made)):
+        m, k = hd.code_params(sp.n)
+        nw = hd.words_for(sp.num_codewords * k)
+        assert np.array_equal(o_h[offs_out[j]:offs_out[j] + nw], eo[:nw]), f"packet {j} (n={sp.n}) data bits"
+        assert np.array_equal(s_h[offs_syn[j]:offs_syn[j] + sp.num_codewords], es), f"packet {j} syndromes"
+        assert e_h[j] == ee, f"packet {j} err_count"

@@ -4,7 +4,7 @@ the allocating entry point hd_decode_batch.
 Some callers cannot allocate device memory: a process that budgets all device
 memory up front, an application whose allocator hooks forbid allocations from
 inside libraries, or a latency-critical receive path where an allocation could
-stall or fail.  For them the library keeps the batch tables in a fixed 1 MiB
+stall or fail.  For them the library keeps the batch tile table in a fixed 1 MiB
 device array.  These tests check that two calls in a row give bit-exactly the
 data bits, syndromes and error counts of hd_decode_batch, and that batches
 beyond the array's limits are refused.
@@ -104,7 +104,8 @@ def test_noalloc_refuses_batches_beyond_its_array():
     # rejected on the host before any device work; the pointers are never used
     too_many_packets = hd.packet_table([(16, 16, None, 1, 7, 0)] * 4097)
     assert hd.hd_decode_batch_noalloc(too_many_packets, 4097, None, None) == hd.HD_ERR_CAPACITY
-    too_many_tiles = hd.packet_table([(16, 16, None, 1024 * 49137, 7, 0)])
+    # n = 7 packs four 1024-codeword chunks per tile; the array holds 16,380 tiles
+    too_many_tiles = hd.packet_table([(16, 16, None, 4096 * 16381, 7, 0)])
     assert hd.hd_decode_batch_noalloc(too_many_tiles, 1, None, None) == hd.HD_ERR_CAPACITY
     bad_n = hd.packet_table([(16, 16, None, 10, 9, 0)])
     assert hd.hd_decode_batch_noalloc(bad_n, 1, None, None) == hd.HD_ERR_INVALID_N
