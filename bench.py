@@ -78,6 +78,55 @@ def dist_setup(gpus):
     return rank, world, local
 
 
+def kernel_sources_hash():
+    """sha256 over the CUDA sources and the public header (names and contents)."""
+    import glob
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_1412_6862_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")) +
+                   glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "hd.h")]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel_desc):
+    """DRAM bytes per launch of the roofline kernel from the committed ncu record,
+    or None when the kernel sources or its configuration changed since."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic_n63.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("sources_sha256") != kernel_sources_hash() or rec.get("kernel") != kernel_desc:
+        return None
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+
+
+def reduce_max(value, device=None):
+    """Max of a float over all ranks (the value itself when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
+def shard_seed(n, rank):
+    """Every rank decodes its own shard: the same workload with rank-specific data."""
+    return n + 1000 * rank
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -386,7 +435,7 @@ def run_ours(args):
     for n in codes:
         m, k = code_params(n)
         N = SWEEP_N
-        seed = n + 1000 * rank
+        seed = shard_seed(n, rank)
         data = synth.random_words(seed, N * k)
         d_data = torch.from_numpy(data.view(np.int32)).to(dev)
         d_in = hd.encode(d_data, n, N)                      # GPU encoder builds the codewords
@@ -462,16 +511,16 @@ def run_ours(args):
         t_end.record(stream_h)
         barrier()
     launches = launches_per_step * args.steps
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(t_start.elapsed_time(t_end), dev)
     bits_per_step = sum(bufs[n]["N"] * bufs[n]["k"] for n in codes)
-    value = bits_per_step * args.steps * world / (ms / 1e3) / 1e9
+    value = weak_scaling_value(bits_per_step * args.steps, world, ms / 1e3) / 1e9
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kern_events]))
     roof_bytes = algorithmic_bytes(roof_n, SWEEP_N)
     peak, peak_kind = peaks()
+    vinfo = hd.hd_variant_current(roof_n, hd.SYN_U8)
+    kernel_desc = (f"k_decode_stream<{roof_n}, 1, {vinfo['threads']}, {vinfo['stages']}, "
+                   f"{vinfo['codewords_per_thread']}, {vinfo['inplace']}>")
+    traffic = recorded_traffic(kernel_desc) if roof_n == ROOFLINE_N else None
     achieved = roof_bytes / (kern_ms / 1e3) / 1e9
     clocks = clk.summary()
 
@@ -499,12 +548,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = bits_per_step * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
+    e2e_s = reduce_max(max(time.perf_counter() - t0, 1e-9), dev)
+    e2e_value = weak_scaling_value(bits_per_step * e2e_steps, world, e2e_s) / 1e9 if e2e_steps else None
 
     batched = None
     if not args.no_batched:
@@ -528,9 +573,9 @@ def run_ours(args):
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (475 MB of streams and outputs, each touched once per step)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"hd_decode n={roof_n}, N=2^24 ({roof_bytes} algorithmic bytes/launch, "
-                                   f"{kern_ms * 1e3:.2f} us avg)", "peak_kind": peak_kind},
+                                   f"{kern_ms * 1e3:.2f} us avg; {kernel_desc})", "peak_kind": peak_kind},
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clocks,
