@@ -221,6 +221,79 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
 hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
                                   void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of arriving packets.
+ *
+ * A server owns a scheduler thread and `max_waves` wave slots (one CUDA
+ * stream each).  Packets already resident in device memory are submitted from
+ * any thread; whenever a slot is free the scheduler admits waiting packets in
+ * arrival order, as many as the slot's limits and the device-memory budget
+ * (in + out + syndrome bytes of admitted, unfinished packets <= mem_cap_bytes)
+ * allow, and launches them as one batched decode on that slot's stream.  Waves
+ * on different slots overlap on the GPU, so packets arriving while others are
+ * being decoded start as soon as a slot and budget free up.  This applies the
+ * paper's asynchronous pipelining of successive packets (Sec. III-B) to
+ * device-resident packets.  Results are exactly those of hd_decode() on each
+ * packet alone.
+ * ------------------------------------------------------------------------- */
+typedef struct hd_server hd_server;
+
+typedef struct {
+    uint32_t max_waves;        /* wave slots (concurrent batched launches), 1..64 */
+    uint32_t max_wave_packets; /* packets per wave */
+    uint32_t max_wave_tiles;   /* tile-table capacity per wave (a packet of N codewords needs <= N/256 + 2) */
+    uint32_t queue_capacity;   /* submitted packets waiting for admission */
+    uint64_t mem_cap_bytes;    /* admission budget in bytes (see above) */
+} hd_server_config;
+
+typedef struct {
+    uint64_t tag;         /* the caller's tag from hd_server_submit */
+    uint64_t err_count;   /* nonzero syndromes in the packet */
+    uint64_t t_submit_ns; /* steady-clock times: submitted, admitted into a wave, completion seen */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;
+    int32_t status;       /* HD_OK, or HD_ERR_CUDA if the wave failed */
+} hd_completion;
+
+typedef struct {
+    uint64_t submitted, completed, rejected; /* rejected: submissions refused because the queue was full */
+    uint64_t waves;                          /* batched launches */
+    uint64_t max_resident_bytes;             /* high-water mark of the admission budget */
+    double mean_wave_packets;
+    /* filled by hd_serve_trace: latency from scheduled arrival to completion */
+    double p50_latency_us, p99_latency_us, max_latency_us;
+    double duration_s;           /* first arrival to last completion */
+    uint64_t backpressure_waits; /* submissions retried because the queue was full */
+} hd_server_stats;
+
+/* Create a server on the current device (allocates its slots: per slot a
+ * stream, an event, a device tile table and pinned staging). */
+hd_status hd_server_create(const hd_server_config *cfg, hd_server **server);
+
+/* Queue one packet (device buffers as in hd_packet; they must stay valid until
+ * its completion is polled).  Thread-safe.  HD_ERR_CAPACITY when the queue is
+ * full or the packet alone exceeds the budget or a wave's tile capacity. */
+hd_status hd_server_submit(hd_server *server, const hd_packet *packet, uint64_t tag);
+
+/* Move up to `max` completions (in completion order) to `out`; *count gets the
+ * number moved.  Returns the server's sticky error, if any. */
+hd_status hd_server_poll(hd_server *server, hd_completion *out, uint32_t max, uint32_t *count);
+
+/* Wait until every submitted packet has completed (HD_ERR_TIMEOUT after timeout_ns). */
+hd_status hd_server_drain(hd_server *server, uint64_t timeout_ns);
+
+hd_status hd_server_get_stats(hd_server *server, hd_server_stats *stats);
+
+/* Finish the admitted and queued packets, stop the scheduler and free the slots. */
+void hd_server_destroy(hd_server *server);
+
+/* Replay an open-loop arrival trace through a fresh server: packet j is
+ * submitted at arrival_s[j] seconds (non-decreasing) after the start, with tag
+ * j; completions[j] receives its completion.  Fills stats including the
+ * p50/p99 latency from scheduled arrival to observed completion. */
+hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *packets, const double *arrival_s,
+                         uint32_t num, hd_completion *completions, hd_server_stats *stats);
+
 /* Human-readable name of a status code (static storage). */
 const char *hd_status_string(hd_status status);
 

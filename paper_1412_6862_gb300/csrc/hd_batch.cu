@@ -19,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "hd_batch_internal.h"
 #include "hd_generic.cuh"
 #include "hd_internal.h"
 #include "hd_stream.cuh"
@@ -37,44 +38,6 @@ struct DevPacket {
     uint32_t syn_type;
     uint32_t pad;
 };
-
-// A self-contained work item: everything a warp needs to decode it, so that
-// the warp never chases a second table.
-struct DevTile {
-    const uint32_t *in;  // packet input (word 0 = codeword 0)
-    uint32_t *out;       // packet output
-    uint8_t *syn;        // packet syndromes (NULL when syn_type is 0)
-    uint64_t num_cw;     // packet length in codewords
-    uint64_t c0;         // first codeword of the tile (a multiple of 32)
-    uint32_t packet;     // index into err_counts
-    uint32_t count;      // codewords, | kFullTile for whole chunks of 32*G decoded by the chunk decoder
-    uint32_t bytes;      // bulk-load size of a full tile (0 for a tail)
-    uint16_t n;
-    uint8_t m;
-    uint8_t syn_type;
-    uint64_t pad;
-};
-
-constexpr uint32_t kFullTile = 0x80000000u;
-
-inline DevTile make_tile(const uint32_t *in, uint32_t *out, uint8_t *syn, uint64_t num_cw, uint32_t n, uint32_t m,
-                         uint32_t syn_type, uint32_t packet, uint64_t c0, uint32_t count, uint32_t bytes)
-{
-    DevTile t;
-    t.in = in;
-    t.out = out;
-    t.syn = syn;
-    t.num_cw = num_cw;
-    t.c0 = c0;
-    t.packet = packet;
-    t.count = count;
-    t.bytes = bytes;
-    t.n = (uint16_t)n;
-    t.m = (uint8_t)m;
-    t.syn_type = (uint8_t)syn_type;
-    t.pad = 0;
-    return t;
-}
 
 // Tails are cut to at most this many codewords (a tail of n >= 7 is shorter
 // than one chunk anyway; n = 3 streams are all tail).
@@ -476,6 +439,35 @@ void drop_graph(hd_plan *p)
 }
 
 }  // namespace
+
+namespace hd {
+
+hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::vector<DevTile> &tiles,
+                           uint64_t *bytes)
+{
+    std::vector<DevPacket> pk;
+    hd_plan stats;
+    const hd_status rc = build_tables(table, num_packets, pk, tiles, &stats);
+    if (rc == HD_OK && bytes) *bytes += stats.in_bytes + stats.out_bytes + stats.syn_bytes;
+    return rc;
+}
+
+cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32_t *d_counter,
+                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st)
+{
+    hd_plan p;
+    p.num_packets = num_packets;
+    p.num_tiles = num_tiles;
+    p.d_tiles = const_cast<DevTile *>(d_tiles);
+    p.d_counter = d_counter;
+    LaunchGeom geom;
+    cudaError_t e = prepare_plan(&p, &geom);
+    if (e == cudaSuccess) e = enqueue_plan(&p, geom, d_err, st);
+    if (e == cudaSuccess && num_tiles) count_launch();
+    return e;
+}
+
+}  // namespace hd
 
 extern "C" {
 

@@ -63,8 +63,34 @@ class PlanInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    """Mirror of hd_server_config."""
+    _fields_ = [("max_waves", _u32), ("max_wave_packets", _u32), ("max_wave_tiles", _u32),
+                ("queue_capacity", _u32), ("mem_cap_bytes", _u64)]
+
+
+class Completion(ctypes.Structure):
+    """Mirror of hd_completion."""
+    _fields_ = [("tag", _u64), ("err_count", _u64), ("t_submit_ns", _u64), ("t_admit_ns", _u64),
+                ("t_done_ns", _u64), ("status", _c.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    """Mirror of hd_server_stats."""
+    _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("waves", _u64),
+                ("max_resident_bytes", _u64), ("mean_wave_packets", _c.c_double), ("p50_latency_us", _c.c_double),
+                ("p99_latency_us", _c.c_double), ("max_latency_us", _c.c_double), ("duration_s", _c.c_double),
+                ("backpressure_waits", _u64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _PKP = _c.POINTER(Packet)
 _PIP = _c.POINTER(PlanInfo)
+_SCP = _c.POINTER(ServerConfig)
+_CMP = _c.POINTER(Completion)
+_SSP = _c.POINTER(ServerStats)
 
 # name -> (restype, argtypes); every entry is declared in include/hd.h
 SIGNATURES = {
@@ -82,6 +108,13 @@ SIGNATURES = {
     "hd_plan_destroy": (None, [_vp]),
     "hd_decode_batch": (_i32, [_PKP, _u32, _vp, _vp]),
     "hd_decode_batch_noalloc": (_i32, [_PKP, _u32, _vp, _vp]),
+    "hd_server_create": (_i32, [_SCP, _c.POINTER(_vp)]),
+    "hd_server_submit": (_i32, [_vp, _PKP, _u64]),
+    "hd_server_poll": (_i32, [_vp, _CMP, _u32, _c.POINTER(_u32)]),
+    "hd_server_drain": (_i32, [_vp, _u64]),
+    "hd_server_get_stats": (_i32, [_vp, _SSP]),
+    "hd_server_destroy": (None, [_vp]),
+    "hd_serve_trace": (_i32, [_SCP, _PKP, _c.POINTER(_c.c_double), _u32, _CMP, _SSP]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -216,6 +249,61 @@ def hd_decode_batch(table, num_packets: int, err_counts, cuda_stream) -> int:
 
 def hd_decode_batch_noalloc(table, num_packets: int, err_counts, cuda_stream) -> int:
     return lib().hd_decode_batch_noalloc(table, num_packets, err_counts, cuda_stream)
+
+
+def server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=65536, queue_capacity=1 << 16,
+                  mem_cap_bytes=4 << 30) -> ServerConfig:
+    return ServerConfig(max_waves, max_wave_packets, max_wave_tiles, queue_capacity, mem_cap_bytes)
+
+
+def hd_serve_trace(cfg: ServerConfig, table, arrival_s, num: int):
+    """Replay an arrival trace; returns (completions array, stats dict)."""
+    import numpy as np
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    comps = (Completion * max(1, num))()
+    st = ServerStats()
+    check(lib().hd_serve_trace(ctypes.byref(cfg), table, arr.ctypes.data_as(_c.POINTER(_c.c_double)), num, comps,
+                               ctypes.byref(st)), "hd_serve_trace")
+    return comps, st.as_dict()
+
+
+class Server:
+    """A continuous-batching server (hd_server_*)."""
+
+    def __init__(self, cfg: ServerConfig | None = None):
+        self.cfg = cfg or server_config()
+        h = _vp()
+        check(lib().hd_server_create(ctypes.byref(self.cfg), ctypes.byref(h)), "hd_server_create")
+        self.handle = h.value
+
+    def submit(self, in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type, tag) -> int:
+        pk = Packet(in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type if syn_ptr else SYN_NONE)
+        return lib().hd_server_submit(self.handle, ctypes.byref(pk), tag)
+
+    def poll(self, max_n: int = 4096):
+        buf = (Completion * max_n)()
+        c = _u32(0)
+        rc = lib().hd_server_poll(self.handle, buf, max_n, ctypes.byref(c))
+        return rc, [buf[i] for i in range(c.value)]
+
+    def drain(self, timeout_s: float = 60.0) -> int:
+        return lib().hd_server_drain(self.handle, int(timeout_s * 1e9))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().hd_server_get_stats(self.handle, ctypes.byref(st)), "hd_server_get_stats")
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.handle:
+            lib().hd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
