@@ -54,6 +54,10 @@ def parse_args():
     ap.add_argument("--batched-only", action="store_true", help="run only the batched mixed-n section")
     ap.add_argument("--batched-packets", type=int, default=10000)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
+    ap.add_argument("--serve-packets", type=int, default=100000)
+    ap.add_argument("--serve-rates", type=str, default="1e4,1e5,1e6", help="Poisson arrival rates, packets/s")
     return ap.parse_args()
 
 
@@ -78,13 +82,15 @@ def dist_setup(gpus):
     return rank, world, local
 
 
+# The sources the roofline kernel (the n = 63 streaming decoder) is compiled from.
+ROOFLINE_SOURCES = ("hd_device.cuh", "hd_tile.cuh", "hd_stream.cuh", "hd_stream_b.cu")
+
+
 def kernel_sources_hash():
-    """sha256 over the CUDA sources and the public header (names and contents)."""
-    import glob
+    """sha256 over the roofline kernel's sources (names and contents)."""
     import hashlib
     pkg = os.path.join(ROOT, "paper_1412_6862_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")) +
-                   glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "hd.h")]
+    files = [os.path.join(pkg, f) for f in ROOFLINE_SOURCES]
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
@@ -340,7 +346,7 @@ def build_batched(dev, num_packets, seed=0, lengths=None):
     return layout, d_in, d_out, d_syn
 
 
-def run_batched(dev, args, peak):
+def run_batched(dev, args, peak, keep_pool=False):
     import torch
     from paper_1412_6862_gb300 import hd
     t_setup = time.perf_counter()
@@ -388,7 +394,7 @@ def run_batched(dev, args, peak):
     del g
     hd.hd_plan_destroy(plan)
     gbps = lambda t: bits / t / 1e9
-    return {
+    res = {
         "workload": f"batched mixed-n: {P} packets, n uniform over {{7,15,31,63,127,255}}, length log-uniform "
                     f"64 bit..4 Mbit rounded to whole codewords, p1={BATCH_P1}, u8 syndromes + per-packet err_count",
         "packets": P, "codewords": int(sum(N for (n, N, *_r) in layout)), "decoded_bits": int(bits),
@@ -402,6 +408,43 @@ def run_batched(dev, args, peak):
         "speedup_vs_per_packet_graph": t_graph / t_pers,
         "setup_s": setup_s,
     }
+    if keep_pool:
+        return res, (layout, d_in, d_out, d_syn)
+    return res
+
+
+def run_serving(dev, args, pool=None):
+    """Open-loop Poisson arrivals of packets from the batched distribution
+    (payloads pre-staged in device memory), served with continuous batching
+    under a 4 GB admission budget: p50/p99 latency and sustained Gbit/s."""
+    from paper_1412_6862_gb300 import hd, synth
+    t_setup = time.perf_counter()
+    layout, d_in, d_out, d_syn = pool if pool is not None else build_batched(dev, args.batched_packets)
+    P = len(layout)
+    bi, bo, bs = d_in.data_ptr(), d_out.data_ptr(), d_syn.data_ptr()
+    rows = [(bi + 4 * oi, bo + 4 * oo, bs + osy, N, n, hd.SYN_U8) for (n, N, oi, oo, osy, od, iw, ow, dw) in layout]
+    bits = [N * code_params(n)[1] for (n, N, *_r) in layout]
+    num = args.serve_packets
+    table = hd.packet_table([rows[j % P] for j in range(num)])
+    cfg = hd.server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=1 << 16,
+                           queue_capacity=max(1 << 16, num), mem_cap_bytes=4 << 30)
+    setup_s = time.perf_counter() - t_setup
+    out = {"workload": f"open-loop Poisson arrivals of packets from the batched distribution ({P}-packet device "
+                       f"pool, cycled), {num} packets per rate; continuous batching with 4 wave slots, <= 4096 "
+                       f"packets per wave, 4 GB admission budget; latency = scheduled arrival -> completion seen "
+                       f"by the host", "setup_s": setup_s, "rates": {}}
+    for rate in (float(r) for r in args.serve_rates.split(",")):
+        arr = synth.poisson_arrivals(int(rate) % 1000003, num, rate)
+        comps, st = hd.hd_serve_trace(cfg, table, arr, num)
+        decoded = sum(bits[j % P] for j in range(num))
+        out["rates"][f"{rate:g}"] = {
+            "p50_latency_us": st["p50_latency_us"], "p99_latency_us": st["p99_latency_us"],
+            "max_latency_us": st["max_latency_us"],
+            "sustained_gbps": decoded / st["duration_s"] / 1e9 if st["duration_s"] > 0 else None,
+            "offered_gbps": decoded / float(arr[-1]) / 1e9, "duration_s": st["duration_s"],
+            "waves": st["waves"], "mean_wave_packets": st["mean_wave_packets"],
+            "max_resident_gb": st["max_resident_bytes"] / 1e9, "backpressure_waits": st["backpressure_waits"]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -424,6 +467,11 @@ def run_ours(args):
         res = run_batched(dev, args, peaks()[0])
         if rank == 0:
             print(json.dumps({"batched": res}), flush=True)
+        return
+    if args.serve_only:
+        res = run_serving(dev, args)
+        if rank == 0:
+            print(json.dumps({"serving": res}), flush=True)
         return
 
     codes = tuple(int(c) for c in args.codes.split(","))
@@ -524,21 +572,19 @@ def run_ours(args):
     achieved = roof_bytes / (kern_ms / 1e3) / 1e9
     clocks = clk.summary()
 
-    # end to end through the public API from pinned host buffers: H2D of each
-    # stream, decode, D2H of data bits, syndromes and err_count, every step
+    # end to end through the C ABI with HOST buffers: hd_decode_host copies each
+    # stream from pinned host memory, decodes it and copies data bits,
+    # syndromes and err_count back, overlapping the copies with the decode
     h2d = sum(bufs[n]["pinned"].numel() * 4 for n in codes)
     d2h = sum(bufs[n]["out"].numel() * 4 + bufs[n]["syn"].numel() + 8 for n in codes)
 
     def e2e_step():
         for n in codes:
             b = bufs[n]
-            b["d_in"].copy_(b["pinned"], non_blocking=True)
-            hd.decode(b["d_in"], n, b["N"], syn_type=hd.SYN_U8, out=b["out"], syndromes=b["syn"],
-                      err_count=b["err"])
-            b["out_h"].copy_(b["out"], non_blocking=True)
-            b["syn_h"].copy_(b["syn"], non_blocking=True)
-            b["err_h"].copy_(b["err"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+            rc, _ = hd.hd_decode_host(b["pinned"].data_ptr(), n * b["N"], n, b["N"], b["out_h"].data_ptr(),
+                                      b["syn_h"].data_ptr(), hd.SYN_U8, 0, 0)
+            if rc != 0:
+                raise hd.HDError(rc, "hd_decode_host")
 
     e2e_steps = 0 if args.no_e2e else args.e2e_steps
     for _ in range(3 if e2e_steps else 0):
@@ -551,13 +597,18 @@ def run_ours(args):
     e2e_s = reduce_max(max(time.perf_counter() - t0, 1e-9), dev)
     e2e_value = weak_scaling_value(bits_per_step * e2e_steps, world, e2e_s) / 1e9 if e2e_steps else None
 
-    batched = None
-    if not args.no_batched:
+    batched = serving = None
+    if not (args.no_batched and args.no_serve):
         for b in bufs.values():  # free the sweep's buffers first
             b.clear()
         bufs.clear()
         torch.cuda.empty_cache()
-        batched = run_batched(dev, args, peak)
+    pool = None
+    if not args.no_batched:
+        batched, pool = run_batched(dev, args, peak, keep_pool=True)
+    if not args.no_serve:
+        serving = run_serving(dev, args, pool)
+    pool = None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -581,6 +632,7 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

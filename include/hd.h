@@ -75,6 +75,22 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
                     uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
                     unsigned long long *err_count, void *cuda_stream);
 
+/* Decode from and to HOST memory with overlapped transfers -- the paper's
+ * asynchronous data transfer (Sec. III-B, Fig. 5, Eq. 1).  The stream is cut
+ * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^20) and each
+ * chunk's host-to-device copy, decode and device-to-host copy run on one of
+ * `depth` CUDA streams (0 = 4, at most 8), so copies in both directions
+ * overlap with the decoding of neighbouring chunks.  Arguments and results are
+ * as in hd_decode(), but host_stream, host_out, host_syndromes and
+ * host_err_count are host memory; pinned (page-locked) buffers are needed for
+ * the copies to overlap, pageable ones work but serialise.  The call is
+ * synchronous: it returns when every result is in host memory.  Device
+ * staging buffers are cached per device and grown on demand; concurrent calls
+ * on one device are serialised. */
+hd_status hd_decode_host(const uint32_t *host_stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                         uint32_t *host_out, void *host_syndromes, hd_syn_type syn_type,
+                         unsigned long long *host_err_count, uint64_t chunk_codewords, uint32_t depth);
+
 /* Encode `num_codewords` messages (the transmitter side of Sec. II: the
  * checksum bits are added to the message).  data_bits holds message i at bits
  * [i*k, (i+1)*k) (device, ceil(num_codewords*k/32) words); stream receives

@@ -116,6 +116,7 @@ SIGNATURES = {
     "hd_server_destroy": (None, [_vp]),
     "hd_serve_trace": (_i32, [_SCP, _PKP, _c.POINTER(_c.c_double), _u32, _CMP, _SSP]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
     "hd_launch_count": (_u64, []),
@@ -170,6 +171,38 @@ def check(status: int, what: str = "") -> None:
 def hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, cuda_stream) -> int:
     return lib().hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
                            cuda_stream)
+
+
+def hd_decode_host(host_stream, in_bits, n, num_codewords, host_out, host_syndromes, syn_type, chunk_codewords=0,
+                   depth=0):
+    """C-ABI mirror taking host pointers (ints); returns (status, err_count)."""
+    err = _c.c_ulonglong(0)
+    rc = lib().hd_decode_host(host_stream, in_bits, n, num_codewords, host_out, host_syndromes, syn_type,
+                              ctypes.byref(err), chunk_codewords, depth)
+    return rc, int(err.value)
+
+
+def decode_host(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U8, out=None, syndromes=None,
+                chunk_codewords: int = 0, depth: int = 0):
+    """Decode host (numpy or CPU-tensor) words; pinned buffers overlap the copies.
+    Returns (out words, syndromes or None, err_count)."""
+    import numpy as np
+    m, k = code_params(n)
+    src = stream_words
+    if out is None:
+        out = np.zeros(max(1, words_for(num_codewords * k)), dtype=np.uint32)
+    if syndromes is None and syn_type != SYN_NONE:
+        syndromes = np.zeros(max(1, num_codewords), dtype=np.uint8 if syn_type == SYN_U8 else np.uint16)
+
+    def ptr(a):
+        if a is None:
+            return None
+        return int(a.data_ptr()) if hasattr(a, "data_ptr") else int(a.ctypes.data)
+
+    rc, err = hd_decode_host(ptr(src), n * num_codewords, n, num_codewords, ptr(out),
+                             ptr(syndromes) if syn_type != SYN_NONE else None, syn_type, chunk_codewords, depth)
+    check(rc, "hd_decode_host")
+    return out, syndromes, err
 
 
 def hd_encode(data_bits, n, num_codewords, stream, cuda_stream) -> int:

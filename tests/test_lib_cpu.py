@@ -82,3 +82,14 @@ def test_plan_validation_host_only(lib):
     assert hd.lib().hd_plan_create(null_syn, 1, ctypes.byref(plan)) == hd.HD_ERR_NULL
     assert hd.lib().hd_plan_create(None, 3, ctypes.byref(plan)) == hd.HD_ERR_NULL
     assert hd.lib().hd_decode_batch(bad_n, 1, None, None) == hd.HD_ERR_INVALID_N
+
+
+def test_host_decode_validation_host_only(lib):
+    import numpy as np
+    z = np.zeros(8, np.uint32)
+    assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 14, 4, z.ctypes.data, None, 0, 0, 0)[0] == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode_host(z.ctypes.data, 15 * 4 + 1, 15, 4, z.ctypes.data, None, 0, 0, 0)[0] == hd.HD_ERR_SIZE
+    assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 15, 4, z.ctypes.data, None, 0, 100, 0)[0] == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 15, 4, z.ctypes.data, None, 0, 128, 9)[0] == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_host(None, 15 * 4, 15, 4, z.ctypes.data, None, 0, 0, 0)[0] == hd.HD_ERR_NULL
+    assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 15, 4, z.ctypes.data, None, 1, 0, 0)[0] == hd.HD_ERR_NULL
