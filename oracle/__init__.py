@@ -65,6 +65,16 @@ class Oracle:
         L.hd_ref_decode.restype = ctypes.c_int
         L.hd_ref_encode.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
         L.hd_ref_encode.restype = ctypes.c_int
+        L.hd_ref_short_checksum_bits.argtypes = [ctypes.c_uint32]
+        L.hd_ref_short_checksum_bits.restype = ctypes.c_int
+        L.hd_ref_decode_short.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, u32p,
+                                          ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.hd_ref_decode_short.restype = ctypes.c_int
+        L.hd_ref_decode_short_range.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, u32p,
+                                                ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.hd_ref_decode_short_range.restype = ctypes.c_int
+        L.hd_ref_encode_short.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
+        L.hd_ref_encode_short.restype = ctypes.c_int
         self.lib = L
         self.path = path
 
@@ -121,6 +131,65 @@ class Oracle:
         err = ctypes.c_uint64(0)
         return self.lib.hd_ref_decode(_u32p(s), in_bits, n, num_codewords, _u32p(out), None,
                                       SYN_NONE, ctypes.byref(err))
+
+    # -- shortened codes (any length n >= 3) --------------------------------
+    def short_params(self, n: int) -> tuple[int, int]:
+        """(r, k) of the shortened code of length n."""
+        r = self.lib.hd_ref_short_checksum_bits(n)
+        if r == 0:
+            raise ValueError(f"unsupported shortened length n={n}")
+        return r, n - r
+
+    def encode_short(self, data_words: np.ndarray, n: int, num_codewords: int) -> np.ndarray:
+        r, k = self.short_params(n)
+        data = np.ascontiguousarray(data_words, dtype=np.uint32)
+        if data.size < words_for(num_codewords * k):
+            raise ValueError("data buffer too small")
+        out = np.zeros(max(1, words_for(num_codewords * n)), dtype=np.uint32)
+        rc = self.lib.hd_ref_encode_short(_u32p(data), n, num_codewords, _u32p(out))
+        if rc != 0:
+            raise RuntimeError(f"hd_ref_encode_short failed: {rc}")
+        return out[:words_for(num_codewords * n)]
+
+    def decode_short(self, stream: np.ndarray, n: int, num_codewords: int, syn_type: int = SYN_U16,
+                     threads: int = 1):
+        """Decode a shortened-code stream: (data words, syndromes, err_count, detected);
+        err_count counts nonzero syndromes, detected those past n."""
+        r, k = self.short_params(n)
+        s = np.ascontiguousarray(stream, dtype=np.uint32)
+        out = np.zeros(max(1, words_for(num_codewords * k)), dtype=np.uint32)
+        syn = None
+        if syn_type == SYN_U8:
+            syn = np.zeros(max(1, num_codewords), dtype=np.uint8)
+        elif syn_type == SYN_U16:
+            syn = np.zeros(max(1, num_codewords), dtype=np.uint16)
+        synp = None if syn is None else syn.ctypes.data_as(ctypes.c_void_p)
+        if threads <= 1 or num_codewords < 64:
+            ce, de = ctypes.c_uint64(0), ctypes.c_uint64(0)
+            rc = self.lib.hd_ref_decode_short(_u32p(s), n * num_codewords, n, num_codewords, _u32p(out), synp,
+                                              syn_type, ctypes.byref(ce), ctypes.byref(de))
+            if rc != 0:
+                raise RuntimeError(f"hd_ref_decode_short failed: {rc}")
+            c, d = int(ce.value), int(de.value)
+        else:
+            per = max(32, ((num_codewords + threads - 1) // threads + 31) // 32 * 32)
+            ranges = [(a, min(per, num_codewords - a)) for a in range(0, num_codewords, per)]
+
+            def run(rg):
+                ce, de = ctypes.c_uint64(0), ctypes.c_uint64(0)
+                rc = self.lib.hd_ref_decode_short_range(_u32p(s), n, rg[0], rg[1], _u32p(out), synp, syn_type,
+                                                        ctypes.byref(ce), ctypes.byref(de))
+                if rc != 0:
+                    raise RuntimeError(f"hd_ref_decode_short_range failed: {rc}")
+                return int(ce.value), int(de.value)
+
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                res = list(ex.map(run, ranges))
+            c, d = sum(x[0] for x in res), sum(x[1] for x in res)
+        out = out[:words_for(num_codewords * k)]
+        if syn is not None:
+            syn = syn[:num_codewords]
+        return out, syn, c, d
 
     def decode_threaded(self, stream: np.ndarray, n: int, num_codewords: int, syn_type: int,
                         threads: int, out: np.ndarray, syn: np.ndarray | None) -> int:
@@ -182,3 +251,15 @@ def decode_rc(stream, in_bits, n, num_codewords):
 
 def decode_threaded(stream, n, num_codewords, syn_type, threads, out, syn):
     return default().decode_threaded(stream, n, num_codewords, syn_type, threads, out, syn)
+
+
+def short_params(n):
+    return default().short_params(n)
+
+
+def encode_short(data_words, n, num_codewords):
+    return default().encode_short(data_words, n, num_codewords)
+
+
+def decode_short(stream, n, num_codewords, syn_type=SYN_U16, threads=1):
+    return default().decode_short(stream, n, num_codewords, syn_type, threads)

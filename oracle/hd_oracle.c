@@ -152,6 +152,113 @@ int hd_ref_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t
     return REF_OK;
 }
 
+/* ---------------------------------------------------------------------------
+ * Shortened codes: any length n >= 3 (the paper's segments of a packet,
+ * Sec. II and Sec. IV-A: a packet of M bytes split into t segments, each with
+ * its own checksum bits).  r = the smallest number of checksum bits with
+ * 2^r >= n + 1; the checksum bits sit at the power-of-two positions <= n.
+ * A syndrome s <= n names the position to flip; s > n names no position, so
+ * the codeword is flagged as detected-uncorrectable and left as received.
+ * ------------------------------------------------------------------------- */
+int hd_ref_short_checksum_bits(uint32_t n)
+{
+    if (n < 3 || n > 65535u) return 0;
+    int r = 0;
+    while ((1u << r) < n + 1u) ++r;
+    return r;
+}
+
+/* Decode codewords [first, first + count) of a shortened-code stream, in the
+ * steps of hd_ref_decode_range; adds the number of nonzero syndromes to
+ * *errs and the number of syndromes past n to *detected. */
+int hd_ref_decode_short_range(const uint32_t *stream, uint32_t n, uint64_t first, uint64_t count, uint32_t *out_bits,
+                              void *syndromes, int syn_type, uint64_t *errs, uint64_t *detected)
+{
+    int r = hd_ref_short_checksum_bits(n);
+    if (r == 0) return REF_ERR_INVALID_N;
+    if (count == 0) return REF_OK;
+    if (!stream || !out_bits || !errs || !detected) return REF_ERR_NULL;
+    uint32_t k = n - (uint32_t)r;
+    static __thread unsigned char bit[65536];
+    uint64_t ce = 0, de = 0;
+    for (uint64_t i = first; i < first + count; ++i) {
+        for (uint32_t p = 1; p <= n; ++p)
+            bit[p] = (unsigned char)get_bit(stream, i * n + p - 1);
+        uint32_t s = 0;
+        for (uint32_t p = 1; p <= n; ++p)
+            if (bit[p]) s ^= p;
+        if (s != 0) {
+            ++ce;
+            if (s <= n)
+                bit[s] ^= 1u; /* names a position: correct it */
+            else
+                ++de; /* names no position: detected, left as received */
+        }
+        uint32_t d = 0;
+        for (uint32_t p = 1; p <= n; ++p) {
+            if (is_checksum_position(p)) continue;
+            put_bit(out_bits, i * k + d, bit[p]);
+            ++d;
+        }
+        if (syn_type == REF_SYN_U8 && syndromes)
+            ((uint8_t *)syndromes)[i] = (uint8_t)s;
+        else if (syn_type == REF_SYN_U16 && syndromes)
+            ((uint16_t *)syndromes)[i] = (uint16_t)s;
+    }
+    *errs += ce;
+    *detected += de;
+    return REF_OK;
+}
+
+int hd_ref_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                        uint32_t *out_bits, void *syndromes, int syn_type, uint64_t *err_count, uint64_t *detected)
+{
+    int r = hd_ref_short_checksum_bits(n);
+    if (r == 0) return REF_ERR_INVALID_N;
+    if (in_bits != (uint64_t)n * num_codewords) return REF_ERR_SIZE;
+    uint64_t ce = 0, de = 0;
+    if (num_codewords > 0) {
+        int rc = hd_ref_decode_short_range(stream, n, 0, num_codewords, out_bits, syndromes, syn_type, &ce, &de);
+        if (rc != REF_OK) return rc;
+        zero_pad(out_bits, num_codewords * (uint64_t)(n - (uint32_t)r));
+    }
+    if (err_count) *err_count = ce;
+    if (detected) *detected = de;
+    return REF_OK;
+}
+
+/* Encoder of the shortened code (test inputs only): as hd_ref_encode, with
+ * the checksum bits at the power-of-two positions <= n. */
+int hd_ref_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream)
+{
+    int r = hd_ref_short_checksum_bits(n);
+    if (r == 0) return REF_ERR_INVALID_N;
+    if (num_codewords == 0) return REF_OK;
+    if (!data_bits || !stream) return REF_ERR_NULL;
+    uint32_t k = n - (uint32_t)r;
+    static __thread unsigned char bit[65536];
+    for (uint64_t i = 0; i < num_codewords; ++i) {
+        uint32_t d = 0;
+        for (uint32_t p = 1; p <= n; ++p) {
+            if (is_checksum_position(p)) {
+                bit[p] = 0;
+            } else {
+                bit[p] = (unsigned char)get_bit(data_bits, i * k + d);
+                ++d;
+            }
+        }
+        uint32_t s = 0;
+        for (uint32_t p = 1; p <= n; ++p)
+            if (bit[p]) s ^= p;
+        for (int j = 0; j < r; ++j)
+            bit[1u << j] = (unsigned char)(1u & (s >> j));
+        for (uint32_t p = 1; p <= n; ++p)
+            put_bit(stream, i * n + p - 1, bit[p]);
+    }
+    zero_pad(stream, num_codewords * (uint64_t)n);
+    return REF_OK;
+}
+
 /* Encoder, used only to build test inputs (Sec. II: the transmitter adds the
  * checksum bits to the message).  Per codeword: the k data bits go to the
  * non-power-of-two positions in increasing order, the checksum positions start

@@ -61,3 +61,37 @@ def decode(stream: np.ndarray, n: int, N: int):
     R[rows, s[rows] - 1] ^= 1
     D = R[:, data_positions(n) - 1]
     return bits_to_words(D.reshape(-1)), s, int(rows.size)
+
+
+# -- shortened codes: any length n, r = the smallest count with 2^r >= n + 1 --
+def short_r(n: int) -> int:
+    r = 0
+    while (1 << r) < n + 1:
+        r += 1
+    return r
+
+
+def short_parity_check_matrix(n: int) -> np.ndarray:
+    """r x n matrix over GF(2): column p-1 holds the binary expansion of p."""
+    r = short_r(n)
+    p = np.arange(1, n + 1)
+    return ((p[None, :] >> np.arange(r)[:, None]) & 1).astype(np.int64)
+
+
+def short_syndromes(stream: np.ndarray, n: int, N: int) -> np.ndarray:
+    H = short_parity_check_matrix(n)
+    R = codeword_matrix(stream, n, N).astype(np.int64)
+    S = (R @ H.T) & 1
+    return (S << np.arange(H.shape[0])[None, :]).sum(axis=1)
+
+
+def short_decode(stream: np.ndarray, n: int, N: int):
+    """Matrix-form decode of a shortened code: a syndrome s <= n flips position
+    s, a larger one flips nothing.  Returns (data words, syndromes, err_count,
+    detected) with err_count = nonzero syndromes, detected = syndromes > n."""
+    R = codeword_matrix(stream, n, N).copy()
+    s = short_syndromes(stream, n, N)
+    fix = np.nonzero((s != 0) & (s <= n))[0]
+    R[fix, s[fix] - 1] ^= 1
+    D = R[:, data_positions(n) - 1]
+    return bits_to_words(D.reshape(-1)), s, int(np.count_nonzero(s)), int(np.count_nonzero(s > n))

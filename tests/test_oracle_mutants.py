@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as pins
+from tests import test_oracle_short as short_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hd_oracle.c")
 
@@ -32,6 +33,19 @@ MUTANTS = {
                                    "put_bit(out_bits, i * k + ((d ^ 1u) < k ? (d ^ 1u) : d), bit[p]);"),
 }
 
+# Mistakes in the shortened-code functions, caught by the pins of
+# ``test_oracle_short.py``.
+SHORT_MUTANTS = {
+    "short_r_too_small": ("while ((1u << r) < n + 1u) ++r;", "while ((1u << r) < n) ++r;"),
+    "short_flip_past_length": ("if (s <= n)\n                bit[s] ^= 1u; /* names a position",
+                               "if (1)\n                bit[s] ^= 1u; /* names a position"),
+    "short_detect_not_counted": ("++de; /* names no position", "; /* names no position"),
+    "short_odd_parity_encoder": ("bit[1u << j] = (unsigned char)(1u & (s >> j));",
+                                 "bit[1u << j] = (unsigned char)(1u & ~(s >> j));"),
+    "short_last_position_skipped": ("for (uint32_t p = 1; p <= n; ++p)\n            if (bit[p]) s ^= p;\n        if (s != 0) {",
+                                    "for (uint32_t p = 1; p < n; ++p)\n            if (bit[p]) s ^= p;\n        if (s != 0) {"),
+}
+
 
 def _pin_suite(o):
     """Run the pins against oracle ``o``; return the names of those that fail."""
@@ -52,11 +66,40 @@ def _pin_suite(o):
     return failed
 
 
+def _short_pin_suite(o):
+    checks = [
+        ("params", lambda: short_pins.test_short_params_are_minimal(o)),
+        ("index_sets_11", lambda: short_pins.test_short_index_sets_match_paper(o)),
+        ("brute_11", lambda: short_pins.test_short_bruteforce(o, 11)),
+        ("padded_100", lambda: short_pins.test_short_equals_zero_padded_full_length(o, 100)),
+        ("matrix_545", lambda: short_pins.test_short_matrix_form_long(o, 545)),
+    ]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:
+            failed.append(name)
+    return failed
+
+
 def test_unmutated_copy_passes(tmp_path):
     src = tmp_path / "hd_oracle.c"
     shutil.copy(SRC, src)
     lib = oracle.build(force=True, src=str(src), out=str(tmp_path / "lib.so"))
     assert _pin_suite(oracle.Oracle(lib)) == []
+    assert _short_pin_suite(oracle.Oracle(lib)) == []
+
+
+@pytest.mark.parametrize("name", sorted(SHORT_MUTANTS))
+def test_short_mutant_is_caught(tmp_path, name):
+    old, new = SHORT_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation anchor not unique: {old}"
+    src = tmp_path / "hd_oracle.c"
+    src.write_text(text.replace(old, new, 1))
+    lib = oracle.build(force=True, src=str(src), out=str(tmp_path / "lib.so"))
+    assert _short_pin_suite(oracle.Oracle(lib)), f"mutant {name} passed every pin"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
