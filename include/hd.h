@@ -100,6 +100,58 @@ hd_status hd_encode(const uint32_t *data_bits, uint32_t n, uint64_t num_codeword
                     void *cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * Shortened codes: segments of any length (Sec. II, Fig. 1: the splitter cuts
+ * a packet of M bytes into t segments, each with its own checksum bits; the
+ * evaluation of Sec. IV-A uses M = 400..2000 bytes and t = 2..6).
+ *
+ * A segment of length n, 3 <= n <= 32767, carries r checksum bits, r the
+ * smallest count with 2^r >= n + 1, at the power-of-two positions 1..2^(r-1),
+ * and k = n - r data bits at the other positions in increasing order; the
+ * full-length codes n = 2^m - 1 are the special case with no unused syndrome
+ * values.  Stream layout, parity sense and ownership are those of hd_decode().
+ * ------------------------------------------------------------------------- */
+
+/* r and k of the shortened code of length n (host only; HD_ERR_INVALID_N
+ * outside 3..32767).  Either output pointer may be NULL. */
+hd_status hd_short_params(uint32_t n, uint32_t *r, uint32_t *k);
+
+/* The paper's splitter sizing (Sec. II): a packet of packet_bytes bytes cut
+ * into t segments gives segments of k = ceil(8 * packet_bytes / t) data bits
+ * and r checksum bits, r the smallest count with 2^r >= k + r + 1, so
+ * n = k + r.  The packet's message is the first 8 * packet_bytes of its t * k
+ * data bits; the rest is zero padding.  HD_ERR_INVALID_ARG for t == 0 or
+ * t > 8 * packet_bytes, HD_ERR_SIZE when n would exceed 32767.  Host only. */
+hd_status hd_segment_params(uint32_t packet_bytes, uint32_t t, uint32_t *n, uint32_t *k, uint32_t *r);
+
+/* Decode `num_codewords` back-to-back segments of length n (a batch of
+ * packets of one size and segment count is one such stream: packet p holds
+ * segments [p*t, (p+1)*t)).
+ *
+ * Arguments as hd_decode(), with n in 3..32767.  Syndrome element i is the
+ * checksum vector of segment i (HD_SYN_U8 is accepted only for n <= 255).
+ * A syndrome s with 1 <= s <= n flips position s; a syndrome s > n names no
+ * position: the segment is left as received and counted in *detected_count
+ * (device, one unsigned long long, or NULL).  *err_count (device or NULL)
+ * counts every nonzero syndrome, detected ones included.  Both counters are
+ * overwritten.  num_codewords == 0 is HD_OK and only zeroes the counters. */
+hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                          uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                          unsigned long long *err_count, unsigned long long *detected_count, void *cuda_stream);
+
+/* Encode `num_codewords` messages of k bits into segments of length n (the
+ * inverse of hd_decode_short; arguments as hd_encode(), n in 3..32767).  The
+ * stream's pad bits past num_codewords * n are written as 0. */
+hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
+                          void *cuda_stream);
+
+/* Segments with k >= 64 are decoded by a tiled kernel compiled in several
+ * configurations (warps per CTA, pipeline stages, stage bytes); these select
+ * one for the current device (ordinal < 0 restores the built-in choice).  The
+ * configuration never changes the result.  Host only. */
+hd_status hd_short_variant_count(uint32_t *count);
+hd_status hd_short_variant_select(int32_t ordinal);
+
+/* ---------------------------------------------------------------------------
  * Kernel configurations and the autotuner.
  *
  * Long streams are decoded by a streaming kernel compiled in several

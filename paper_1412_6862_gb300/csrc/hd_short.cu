@@ -1,0 +1,667 @@
+// hd_short.cu -- shortened Hamming codes: segments of any length n.
+//
+// The paper's decoder splits a packet of M bytes into t segments (Sec. II,
+// Fig. 1; the evaluation of Sec. IV-A sweeps M = 400..2000 bytes and
+// t = 2..6), and each segment carries its own checksum bits, so a segment is
+// a codeword of a shortened code: n = k + r bits, r the smallest count with
+// 2^r >= n + 1, checksum bits at the power-of-two positions 1..2^(r-1), data at
+// the other positions.  A syndrome s <= n names the position to flip; a
+// syndrome past n names none, and the codeword is counted as detected and
+// left as received.
+//
+// Two decoders:
+//  * k_short_tiles (k >= 64, i.e. n >= 71): each warp streams tiles of g whole
+//    codewords through a ring of shared-memory stages filled by 1-D bulk
+//    copies.  Per tile it computes the syndromes (teams of T lanes per
+//    codeword, one redux per team), applies the corrections in the stage,
+//    then builds the output words directly: every 32-bit output word is at
+//    most two runs of one codeword's stage bits (the runs between checksum
+//    positions are at least 31 bits long past data bit 26), plus the
+//    codeword's first 32 data bits taken from a per-codeword head word.
+//  * k_short_small (n <= 255): warp tiles of 32 codewords straight from global
+//    memory, one codeword per lane, like the generic full-length kernel.
+// The encoder (k_encode_short) is bit-serial, one thread per codeword: it is
+// used to build inputs, not timed.
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "hd_device.cuh"
+#include "hd_generic.cuh"
+#include "hd_internal.h"
+
+namespace hd {
+namespace {
+
+constexpr uint32_t kShortMaxN = 32767;  // r <= 15: syndromes fit 16 bits
+constexpr uint32_t kLongMinK = 64;      // k_short_tiles needs the first 58 data bits inside one codeword
+
+__host__ __device__ inline uint32_t short_r(uint32_t n)
+{
+    uint32_t r = 0;
+    while ((1u << r) < n + 1u) ++r;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t lowmask(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : (1u << b) - 1u; }
+
+// Low five syndrome bits from the XOR of a codeword's position-domain words:
+// bit i is the parity of the bits whose in-word index has bit i set.
+__device__ __forceinline__ uint32_t fold5(uint32_t f)
+{
+    return (__popc(f & 0xAAAAAAAAu) & 1u) | ((__popc(f & 0xCCCCCCCCu) & 1u) << 1) |
+           ((__popc(f & 0xF0F0F0F0u) & 1u) << 2) | ((__popc(f & 0xFF00FF00u) & 1u) << 3) |
+           ((__popc(f & 0xFFFF0000u) & 1u) << 4);
+}
+
+struct ShortArgs {
+    const uint32_t *in;
+    uint32_t *out;
+    void *syn;
+    unsigned long long *err;
+    unsigned long long *det;
+    uint32_t *status;
+    uint64_t num_cw;
+    uint64_t in_words;
+    uint64_t bulk_end;  // bytes of the input that 16-byte bulk copies may read
+    uint64_t ntiles;
+    uint32_t n, k, g;   // code length, data bits, codewords per tile
+    uint32_t Y;         // position-domain words per codeword: ceil((n + 1) / 32)
+    uint32_t ylast;     // valid-bit mask of the last position-domain word
+    uint32_t tlog;      // log2 of the team size of the syndrome pass
+    int syn_type;
+    float kinv;         // 1 / k, for the quotient estimate of the output pass
+};
+
+template <int SB>
+struct TileGeom {
+    // stage: 16-byte guard word area (read as word -1), SB data bytes, 16 bytes of slack
+    static constexpr uint32_t stage_stride = SB + 32;
+    static constexpr uint32_t max_g = 256;
+};
+
+// Codewords per tile: the tile's input plus 16-byte rounding at both ends fits SB bytes.
+template <int SB>
+inline uint32_t tile_codewords(uint32_t n)
+{
+    const uint32_t g = (uint32_t)((8u * SB - 256u) / n);
+    return std::min<uint32_t>(g, TileGeom<SB>::max_g);
+}
+
+// Bytes of tile t that a bulk copy brings in, and where they start.
+__device__ __forceinline__ void tile_span(const ShortArgs &a, uint64_t t, uint64_t &byte0, uint32_t &bytes,
+                                          uint32_t &gcnt)
+{
+    const uint64_t c0 = t * a.g;
+    gcnt = (uint32_t)min((uint64_t)a.g, a.num_cw - c0);
+    const uint64_t bit0 = c0 * a.n, bit1 = (c0 + gcnt) * a.n;
+    byte0 = (bit0 >> 7) << 4;
+    uint64_t byte1 = ((bit1 + 127) >> 7) << 4;
+    if (byte1 > a.bulk_end) byte1 = a.bulk_end;
+    bytes = byte1 > byte0 ? (uint32_t)(byte1 - byte0) : 0u;
+}
+
+template <int SB>
+__device__ __forceinline__ void issue_tile(const ShortArgs &a, uint64_t t, uint8_t *stage, uint64_t *bar)
+{
+    uint64_t byte0;
+    uint32_t bytes, gcnt;
+    tile_span(a, t, byte0, bytes, gcnt);
+    mbar_arrive_expect_tx(bar, bytes);
+    if (bytes) bulk_g2s(stage + 16, reinterpret_cast<const uint8_t *>(a.in) + byte0, bytes, bar);
+}
+
+// 32 data bits of codeword c starting at data bit d (d + 32 <= k, d >= 26 or
+// taken through the head word).  cb: stage bit of position 1 of codeword c.
+__device__ __forceinline__ uint32_t data_word(const uint32_t *st, uint32_t cb, uint32_t d, uint32_t head_c)
+{
+    const bool head = d < 26;
+    const uint32_t dx = head ? 32u : d;
+    // dx lies in data run J: positions 2^J + 1 .. 2^(J+1) - 1, data bit dx at position dx + J + 2
+    const uint32_t J1 = 31u - __clz(dx);
+    const uint32_t J = J1 + ((dx + J1 + 2u) >> (J1 + 1u));
+    const uint32_t q = cb + dx + J + 1u;
+    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1];
+    const uint32_t sh = q & 31u;
+    const uint32_t a = __funnelshift_r(lo, hi, sh);
+    const uint32_t b = __funnelshift_rc(lo, hi, sh + 1u);  // skips the checksum position 2^(J+1)
+    const uint32_t r1 = (2u << J) - J - 2u - dx;            // data bits before that position
+    const uint32_t lm = lowmask(r1);
+    uint32_t v = (a & lm) | (b & ~lm);
+    if (head) v = d == 0 ? head_c : (head_c >> d) | (v << (32u - d));
+    return v;
+}
+
+template <int W, int S, int SB>
+__global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
+{
+    using Geom = TileGeom<SB>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr uint32_t warp_bytes = S * Geom::stage_stride + Geom::max_g * 4 + 16 * S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *wbase = smem + warp * warp_bytes;
+    uint32_t *heads = reinterpret_cast<uint32_t *>(wbase + S * Geom::stage_stride);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + S * Geom::stage_stride + Geom::max_g * 4);
+    const uint64_t gw = (uint64_t)blockIdx.x * W + warp, tw = (uint64_t)gridDim.x * W;
+
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+        for (int s = 0; s < S; ++s) {
+            const uint64_t t = gw + (uint64_t)s * tw;
+            if (t < a.ntiles) issue_tile<SB>(a, t, wbase + s * Geom::stage_stride, &bar[s]);
+        }
+    }
+    __syncwarp();
+
+    const uint32_t T = 1u << a.tlog, tl = lane & (T - 1u), team = lane >> a.tlog, G = 32u >> a.tlog;
+    const uint32_t tmask = T == 32 ? 0xFFFFFFFFu : ((1u << T) - 1u) << (team * T);
+    const uint32_t n = a.n, k = a.k;
+    uint32_t errs = 0, dets = 0, it = 0;
+    bool aborted = false;
+    for (uint64_t t = gw; t < a.ntiles; t += tw, ++it) {
+        const int s = (int)(it % S);
+        const bool ok = mbar_wait_bounded(&bar[s], (it / S) & 1u);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            aborted = true;
+            break;
+        }
+        uint8_t *stage = wbase + s * Geom::stage_stride;
+        uint32_t *st = reinterpret_cast<uint32_t *>(stage + 16);
+        uint64_t byte0;
+        uint32_t bytes, gcnt;
+        tile_span(a, t, byte0, bytes, gcnt);
+        const uint64_t c0 = t * a.g;
+        const uint32_t off0 = (uint32_t)((c0 * n) & 127u);
+        // words past the last 16-byte boundary of the input arrive by plain loads
+        {
+            const uint64_t w0 = byte0 >> 2, wb = (byte0 + bytes) >> 2;
+            const uint64_t we = min(((c0 + gcnt) * n + 31) >> 5, a.in_words);
+            for (uint64_t w = wb + lane; w < we; w += 32) st[w - w0] = a.in[w];
+        }
+        __syncwarp();
+
+        // 1. syndromes: team `team` takes codeword cb + team, lane tl its words j = tl, tl + T, ...
+        for (uint32_t cbase = 0; cbase < gcnt; cbase += G) {
+            const uint32_t c = cbase + team;
+            uint32_t x = 0, h = 0;
+            if (c < gcnt) {
+                const int32_t ybase = (int32_t)(off0 + c * n) - 1;  // stage bit of position 0
+                for (uint32_t j = tl; j < a.Y; j += T) {
+                    const int32_t q = ybase + 32 * (int32_t)j;
+                    const int32_t wi = q >> 5;  // -1 reads the guard word
+                    uint32_t w = __funnelshift_r(st[wi], st[wi + 1], (uint32_t)q & 31u);
+                    if (j == 0) w &= ~1u;
+                    if (j == a.Y - 1) w &= a.ylast;
+                    x ^= w;
+                    h ^= (__popc(w) & 1u) ? j : 0u;
+                }
+            }
+            x = __reduce_xor_sync(tmask, x);
+            h = __reduce_xor_sync(tmask, h);
+            if (tl == 0 && c < gcnt) {
+                const uint32_t syn = (h << 5) | fold5(x);
+                if (syn != 0) {
+                    ++errs;
+                    if (syn <= n) {
+                        const uint32_t b = off0 + c * n + syn - 1u;
+                        atomicXor(&st[b >> 5], 1u << (b & 31u));
+                    } else {
+                        ++dets;
+                    }
+                }
+                if (a.syn_type == 1) static_cast<uint8_t *>(a.syn)[c0 + c] = (uint8_t)syn;
+                if (a.syn_type == 2) static_cast<uint16_t *>(a.syn)[c0 + c] = (uint16_t)syn;
+            }
+        }
+        __syncwarp();
+
+        // 2. head words: data bits 0..31 of each codeword (positions 3, 5-7, 9-15, 17-31, 33-38)
+        for (uint32_t c = lane; c < gcnt; c += 32) {
+            const int32_t q = (int32_t)(off0 + c * n) - 1;
+            const int32_t wi = q >> 5;
+            const uint32_t sh = (uint32_t)q & 31u;
+            const uint32_t y0 = __funnelshift_r(st[wi], st[wi + 1], sh);
+            const uint32_t y1 = __funnelshift_r(st[wi + 1], st[wi + 2], sh);
+            heads[c] = ((y0 >> 3) & 1u) | ((y0 >> 4) & 0xEu) | ((y0 >> 5) & 0x7F0u) | ((y0 >> 6) & 0x3FFF800u) |
+                       ((y1 << 25) & 0xFC000000u);
+        }
+        __syncwarp();
+
+        // 3. output words, four consecutive per lane (one 16-byte store when all are owned)
+        const uint64_t ob0 = c0 * k, ob1 = (c0 + gcnt) * k;
+        const uint64_t F = ob0 >> 5, L = (ob1 - 1) >> 5;
+        const bool fs = (ob0 & 31u) != 0, ls = (ob1 & 31u) != 0 && (c0 + gcnt) < a.num_cw;
+        const uint64_t Fo = F + (fs ? 1 : 0), Lo = L - (ls ? 1 : 0);  // fully owned words
+        for (uint64_t qw = (F & ~3ull) + 4u * lane; qw <= L; qw += 128) {
+            uint32_t v[4];
+            // tile output bit of the quad's first word; words before the tile's first word
+            // are skipped and the tile's first word, if shared, holds only data bits of codeword 0
+            const int64_t e0 = (int64_t)(qw << 5) - (int64_t)ob0;
+            uint32_t c = 0, d = 0;
+            bool placed = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = e0 + 32 * u;
+                uint32_t val = 0;
+                if (e < 0) {
+                    if (e > -32) val = heads[0] << (uint32_t)(-e);
+                } else if (qw + u <= L) {
+                    if (!placed) {  // codeword and data bit of tile output bit e
+                        const uint32_t eu = (uint32_t)e;
+                        c = (uint32_t)((float)eu * a.kinv);
+                        if (c * k > eu) --c;
+                        if ((c + 1) * k <= eu) ++c;
+                        d = eu - c * k;
+                        placed = true;
+                    }
+                    const uint32_t cb = off0 + c * n;
+                    val = data_word(st, cb, d, heads[c]);
+                    const uint32_t rem = k - d;
+                    if (rem < 32) val = (val & lowmask(rem)) | (c + 1 < gcnt ? heads[c + 1] << rem : 0u);
+                    d += 32;
+                    if (d >= k) {
+                        d -= k;
+                        ++c;
+                    }
+                }
+                v[u] = val;
+            }
+            if (qw >= Fo && qw + 3 <= Lo) {
+                *reinterpret_cast<uint4 *>(a.out + qw) = make_uint4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint64_t wq = qw + u;
+                    if (wq < F || wq > L) continue;
+                    if (wq >= Fo && wq <= Lo) {
+                        a.out[wq] = v[u];
+                    } else {
+                        // shared with the neighbouring tile: touch only this tile's bits
+                        const uint32_t own = (wq == F && fs) ? ~lowmask((uint32_t)(ob0 & 31u))
+                                                             : lowmask((uint32_t)(ob1 & 31u));
+                        atomicAnd(&a.out[wq], v[u] | ~own);
+                        atomicOr(&a.out[wq], v[u] & own);
+                    }
+                }
+            }
+        }
+        // the corrections wrote the stage through the generic proxy; the refill writes it through the async one
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            const uint64_t tn = t + (uint64_t)S * tw;
+            if (tn < a.ntiles) issue_tile<SB>(a, tn, stage, &bar[s]);
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && aborted) {
+        atomicOr(a.status, (uint32_t)HD_ERR_TIMEOUT);
+        for (uint32_t j = it; j < it + S; ++j) {
+            const uint64_t tj = gw + (uint64_t)j * tw;
+            if (tj < a.ntiles) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
+        dets += __shfl_xor_sync(0xFFFFFFFFu, dets, o);
+    }
+    if (lane == 0) {
+        if (a.err && errs) atomicAdd(a.err, (unsigned long long)errs);
+        if (a.det && dets) atomicAdd(a.det, (unsigned long long)dets);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Short segments (n <= 255): warp tiles of 32 codewords, one per lane.
+// 32 codewords of any length n fill exactly n input words and k output words.
+// ---------------------------------------------------------------------------
+constexpr int kSmallWarps = 8;
+
+__global__ void __launch_bounds__(kSmallWarps * 32)
+    k_short_small(const uint32_t *__restrict__ in, uint64_t in_words, uint32_t n, uint32_t r, uint64_t num_cw,
+                  uint32_t *__restrict__ out, uint64_t out_words, void *__restrict__ syn, int syn_type,
+                  unsigned long long *__restrict__ err, unsigned long long *__restrict__ det)
+{
+    __shared__ uint32_t sy[kSmallWarps][kWarpSlotWords];
+    __shared__ uint32_t sd[kSmallWarps][kWarpSlotWords];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    uint32_t *my_y = &sy[wp][lane * kSlot];
+    uint32_t *my_d = &sd[wp][lane * kSlot];
+    const uint32_t k = n - r;
+    const uint32_t wy = (n + 32) >> 5;  // ceil((n + 1) / 32)
+    const uint32_t ylast = lowmask(n + 1 - 32 * (wy - 1));
+    const uint64_t tiles = (num_cw + 31) / 32;
+    uint32_t errs = 0, dets = 0;
+    for (uint64_t t = (uint64_t)blockIdx.x * kSmallWarps + wp; t < tiles; t += (uint64_t)gridDim.x * kSmallWarps) {
+        const uint64_t i = t * 32 + lane;
+        const bool valid = i < num_cw;
+        uint32_t y[8];
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w)
+            y[w] = (valid && w < wy) ? load_window(in, in_words, (int64_t)(i * n) - 1 + 32 * (int64_t)w) : 0u;
+        y[0] &= ~1u;
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w)
+            if (w == wy - 1) y[w] &= ylast;
+        const uint32_t s = syndrome_y(y, wy);
+        const uint32_t fix = s <= n ? s : 0u;  // a syndrome past n names no position
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w)
+            if (w < wy) y[w] ^= shl_clamp(fix != 0 ? 1u : 0u, fix - 32u * w);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            my_y[w] = y[w];
+            my_d[w] = 0;
+        }
+        my_y[8] = 0;
+        my_d[8] = 0;
+        // data run j: positions 2^j + 1 .. min(2^(j+1) - 1, n)
+        for (uint32_t j = 1; j < r; ++j) {
+            const uint32_t first = (1u << j) + 1u, last = min((2u << j) - 1u, n);
+            if (last >= first) copy_bits(my_y, first, my_d, (1u << j) - j - 1u, last - first + 1u);
+        }
+        __syncwarp();
+        for (uint32_t q = lane; q < k; q += 32) {
+            const uint64_t g = t * k + q;
+            if (g >= out_words) break;
+            uint32_t c = (32u * q) / k, o = 32u * q - c * k, v = 0, filled = 0;
+            while (filled < 32 && c < 32) {
+                const uint32_t avail = k - o, take = avail < 32 - filled ? avail : 32 - filled;
+                v |= get_bits(&sd[wp][c * kSlot], o, take) << filled;
+                filled += take;
+                ++c;
+                o = 0;
+            }
+            out[g] = v;
+        }
+        if (valid) {
+            if (syn_type == 1) static_cast<uint8_t *>(syn)[i] = (uint8_t)s;
+            if (syn_type == 2) static_cast<uint16_t *>(syn)[i] = (uint16_t)s;
+        }
+        errs += __popc(__ballot_sync(0xFFFFFFFFu, valid && s != 0));
+        dets += __popc(__ballot_sync(0xFFFFFFFFu, valid && s > n));
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (err && errs) atomicAdd(err, (unsigned long long)errs);
+        if (det && dets) atomicAdd(det, (unsigned long long)dets);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Encoder: one thread per codeword, bit-serial.  The stream must be zero.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_pow2(uint32_t p) { return (p & (p - 1u)) == 0; }
+
+__global__ void k_encode_short(const uint32_t *__restrict__ data, uint64_t data_words, uint32_t n, uint32_t r,
+                               uint64_t num_cw, uint32_t *__restrict__ stream)
+{
+    const uint32_t k = n - r;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < num_cw;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        // checksum vector of the message placed at the data positions
+        uint32_t s = 0, d = 0, win = 0;
+        for (uint32_t p = 3; p <= n; ++p) {
+            if (is_pow2(p)) continue;
+            if ((d & 31u) == 0) win = load_window(data, data_words, (int64_t)(c * k + d));
+            if ((win >> (d & 31u)) & 1u) s ^= p;
+            ++d;
+        }
+        // write positions 1..n: checksum bit j at position 2^j makes the syndrome 0
+        const uint64_t b0 = c * n, b1 = b0 + n;
+        uint32_t acc = 0;
+        d = 0;
+        for (uint32_t p = 1; p <= n; ++p) {
+            uint32_t bit;
+            if (is_pow2(p)) {
+                bit = (s >> (31u - __clz(p))) & 1u;
+            } else {
+                if ((d & 31u) == 0) win = load_window(data, data_words, (int64_t)(c * k + d));
+                bit = (win >> (d & 31u)) & 1u;
+                ++d;
+            }
+            const uint64_t b = b0 + p - 1;
+            acc |= bit << (b & 31u);
+            if ((b & 31u) == 31u || p == n) {
+                const uint64_t w = b >> 5;
+                if ((w << 5) >= b0 && (w << 5) + 32 <= b1)
+                    stream[w] = acc;
+                else if (acc)
+                    atomicOr(&stream[w], acc);
+                acc = 0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variant table of the tile kernel (compiled configurations).
+// ---------------------------------------------------------------------------
+struct ShortVariant {
+    int W, S, SB;
+    uint32_t smem;
+    const void *kernel;
+    void (*launch)(const ShortArgs &, int grid, cudaStream_t);
+};
+
+template <int W, int S, int SB>
+void launch_tiles(const ShortArgs &a, int grid, cudaStream_t st)
+{
+    constexpr uint32_t warp_bytes = S * TileGeom<SB>::stage_stride + TileGeom<SB>::max_g * 4 + 16 * S;
+    k_short_tiles<W, S, SB><<<grid, W * 32, W * warp_bytes, st>>>(a);
+}
+
+template <int W, int S, int SB>
+ShortVariant make_short_variant()
+{
+    constexpr uint32_t warp_bytes = S * TileGeom<SB>::stage_stride + TileGeom<SB>::max_g * 4 + 16 * S;
+    return ShortVariant{W, S, SB, W * warp_bytes, reinterpret_cast<const void *>(k_short_tiles<W, S, SB>),
+                        &launch_tiles<W, S, SB>};
+}
+
+const ShortVariant kShortVariants[] = {
+    make_short_variant<4, 2, 8192>(),
+    make_short_variant<4, 3, 4096>(),
+    make_short_variant<8, 2, 4096>(),
+    make_short_variant<4, 4, 2048>(),
+};
+constexpr int kNumShortVariants = sizeof(kShortVariants) / sizeof(kShortVariants[0]);
+
+std::mutex g_short_mu;
+int g_short_bps[64][kNumShortVariants];  // resident CTAs per SM, 0 = not configured
+int g_short_choice[64] = {};             // selected variant per device (index + 1; 0 = default)
+
+int short_blocks_per_sm(int v)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    if (g_short_bps[dev][v] == 0) {
+        const ShortVariant &sv = kShortVariants[v];
+        if (cudaFuncSetAttribute(sv.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv.smem) !=
+            cudaSuccess)
+            return -1;
+        int bps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sv.kernel, sv.W * 32, sv.smem) != cudaSuccess ||
+            bps <= 0)
+            return -1;
+        g_short_bps[dev][v] = bps;
+    }
+    return g_short_bps[dev][v];
+}
+
+int current_short_variant()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    return g_short_choice[dev] > 0 ? g_short_choice[dev] - 1 : 0;
+}
+
+uint32_t team_log(uint32_t Y)
+{
+    // the team size (8, 16 or 32 lanes) that wastes the fewest lane slots; ties go to the larger team
+    uint32_t best = 5, best_slots = (Y + 31) / 32 * 32;
+    for (uint32_t lg = 4; lg >= 3; --lg) {
+        const uint32_t T = 1u << lg, slots = (Y + T - 1) / T * T;
+        if (slots < best_slots) {
+            best = lg;
+            best_slots = slots;
+        }
+    }
+    return best;
+}
+
+cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
+                               int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st)
+{
+    const ShortVariant &v = kShortVariants[vi];
+    const int bps = short_blocks_per_sm(vi);
+    if (bps <= 0) return cudaErrorInvalidConfiguration;
+    const uint32_t r = short_r(n), k = n - r;
+    ShortArgs a{};
+    a.in = in;
+    a.out = out;
+    a.syn = syn;
+    a.err = err;
+    a.det = det;
+    a.status = status_ptr();
+    if (!a.status) return cudaErrorUnknown;
+    a.num_cw = num_cw;
+    a.in_words = words_for_bits(num_cw * n);
+    a.bulk_end = (a.in_words * 4) >> 4 << 4;
+    a.n = n;
+    a.k = k;
+    switch (v.SB) {
+        case 8192: a.g = tile_codewords<8192>(n); break;
+        case 4096: a.g = tile_codewords<4096>(n); break;
+        default: a.g = tile_codewords<2048>(n); break;
+    }
+    if (a.g == 0) return cudaErrorInvalidValue;  // the caller picks a configuration whose stage holds a codeword
+    a.ntiles = (num_cw + a.g - 1) / a.g;
+    a.Y = (n + 32) / 32;
+    const uint32_t lastbits = n + 1 - 32 * (a.Y - 1);
+    a.ylast = lastbits >= 32 ? 0xFFFFFFFFu : (1u << lastbits) - 1u;
+    a.tlog = team_log(a.Y);
+    a.syn_type = syn ? syn_type : 0;
+    a.kinv = 1.0f / (float)k;
+    const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
+    const uint64_t want = (a.ntiles + v.W - 1) / v.W;
+    const int grid = (int)std::min(want, cap);
+    v.launch(a, grid, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace hd
+
+using namespace hd;
+
+namespace {
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+}  // namespace
+
+extern "C" {
+
+hd_status hd_short_params(uint32_t n, uint32_t *r, uint32_t *k)
+{
+    if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
+    const uint32_t rr = short_r(n);
+    if (r) *r = rr;
+    if (k) *k = n - rr;
+    return HD_OK;
+}
+
+hd_status hd_segment_params(uint32_t packet_bytes, uint32_t t, uint32_t *n, uint32_t *k, uint32_t *r)
+{
+    if (packet_bytes == 0 || t == 0 || t > 8u * packet_bytes) return HD_ERR_INVALID_ARG;
+    const uint64_t kk = (8ull * packet_bytes + t - 1) / t;  // data bits per segment
+    uint32_t rr = 0;
+    while ((1ull << rr) < kk + rr + 1) ++rr;
+    const uint64_t nn = kk + rr;
+    if (nn < 3 || nn > kShortMaxN) return HD_ERR_SIZE;
+    if (n) *n = (uint32_t)nn;
+    if (k) *k = (uint32_t)kk;
+    if (r) *r = rr;
+    return HD_OK;
+}
+
+hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                          uint32_t *out_bits, void *syndromes, hd_syn_type syn_type, unsigned long long *err_count,
+                          unsigned long long *detected_count, void *cuda_stream)
+{
+    if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
+    if (syn_type != HD_SYN_NONE && syn_type != HD_SYN_U8 && syn_type != HD_SYN_U16) return HD_ERR_INVALID_ARG;
+    if (syn_type == HD_SYN_U8 && n > 255) return HD_ERR_INVALID_ARG;
+    if (num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+    if (in_bits != (uint64_t)n * num_codewords) return HD_ERR_SIZE;
+    if (num_codewords != 0) {
+        if (!stream || !out_bits) return HD_ERR_NULL;
+        if (syn_type != HD_SYN_NONE && !syndromes) return HD_ERR_NULL;
+        if (!aligned16(stream) || !aligned16(out_bits) || (syndromes && !aligned16(syndromes))) return HD_ERR_ALIGN;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
+    if (detected_count && cudaMemsetAsync(detected_count, 0, sizeof(*detected_count), st) != cudaSuccess)
+        return HD_ERR_CUDA;
+    if (num_codewords == 0) return HD_OK;
+    const uint32_t r = short_r(n), k = n - r;
+    const int syn = syndromes ? (int)syn_type : 0;
+    if (k >= kLongMinK) {
+        int vi = current_short_variant();
+        if (kShortVariants[vi].SB * 8u < n + 256u) vi = 0;  // stage too small for one codeword: largest stage
+        if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
+                               st) != cudaSuccess)
+            return HD_ERR_CUDA;
+        return HD_OK;
+    }
+    const uint64_t tiles = (num_codewords + 31) / 32;
+    const uint64_t want = (tiles + kSmallWarps - 1) / kSmallWarps, cap = (uint64_t)num_sms() * 8;
+    k_short_small<<<(int)std::min(want, cap), kSmallWarps * 32, 0, st>>>(
+        stream, words_for_bits(in_bits), n, r, num_codewords, out_bits, words_for_bits(num_codewords * k),
+        syndromes, syn, err_count, detected_count);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
+                          void *cuda_stream)
+{
+    if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
+    if (num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+    if (num_codewords == 0) return HD_OK;
+    if (!data_bits || !stream) return HD_ERR_NULL;
+    if (!aligned16(data_bits) || !aligned16(stream)) return HD_ERR_ALIGN;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const uint32_t r = short_r(n), k = n - r;
+    if (cudaMemsetAsync(stream, 0, words_for_bits(num_codewords * n) * 4, st) != cudaSuccess) return HD_ERR_CUDA;
+    const uint64_t want = (num_codewords + 255) / 256, cap = (uint64_t)num_sms() * 16;
+    k_encode_short<<<(int)std::min(want, cap), 256, 0, st>>>(data_bits, words_for_bits(num_codewords * k), n, r,
+                                                             num_codewords, stream);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_short_variant_count(uint32_t *count)
+{
+    if (!count) return HD_ERR_NULL;
+    *count = (uint32_t)kNumShortVariants;
+    return HD_OK;
+}
+
+hd_status hd_short_variant_select(int32_t ordinal)
+{
+    if (ordinal >= kNumShortVariants) return HD_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    g_short_choice[dev] = ordinal < 0 ? 0 : ordinal + 1;
+    return HD_OK;
+}
+
+}  // extern "C"

@@ -116,6 +116,12 @@ SIGNATURES = {
     "hd_server_destroy": (None, [_vp]),
     "hd_serve_trace": (_i32, [_SCP, _PKP, _c.POINTER(_c.c_double), _u32, _CMP, _SSP]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_short_params": (_i32, [_u32, _c.POINTER(_u32), _c.POINTER(_u32)]),
+    "hd_segment_params": (_i32, [_u32, _u32, _c.POINTER(_u32), _c.POINTER(_u32), _c.POINTER(_u32)]),
+    "hd_decode_short": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "hd_encode_short": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_short_variant_count": (_i32, [_c.POINTER(_u32)]),
+    "hd_short_variant_select": (_i32, [_c.c_int32]),
     "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -434,6 +440,74 @@ def decode(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U8, out
                    _stream_handle(cuda_stream))
     check(rc, "hd_decode")
     return out, syndromes, err_count
+
+
+def hd_short_params(n: int) -> tuple[int, int]:
+    """(r, k) of the shortened code of length n."""
+    r, k = _u32(0), _u32(0)
+    check(lib().hd_short_params(n, ctypes.byref(r), ctypes.byref(k)), f"hd_short_params n={n}")
+    return int(r.value), int(k.value)
+
+
+def hd_segment_params(packet_bytes: int, t: int) -> tuple[int, int, int]:
+    """(n, k, r) of the segments of a packet of packet_bytes bytes split into t."""
+    n, k, r = _u32(0), _u32(0), _u32(0)
+    check(lib().hd_segment_params(packet_bytes, t, ctypes.byref(n), ctypes.byref(k), ctypes.byref(r)),
+          f"hd_segment_params M={packet_bytes} t={t}")
+    return int(n.value), int(k.value), int(r.value)
+
+
+def hd_decode_short(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, detected_count,
+                    cuda_stream) -> int:
+    return lib().hd_decode_short(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
+                                 detected_count, cuda_stream)
+
+
+def hd_encode_short(data_bits, n, num_codewords, stream, cuda_stream) -> int:
+    return lib().hd_encode_short(data_bits, n, num_codewords, stream, cuda_stream)
+
+
+def hd_short_variant_count() -> int:
+    c = _u32(0)
+    check(lib().hd_short_variant_count(ctypes.byref(c)), "hd_short_variant_count")
+    return int(c.value)
+
+
+def hd_short_variant_select(ordinal: int) -> None:
+    check(lib().hd_short_variant_select(ordinal), "hd_short_variant_select")
+
+
+def decode_short(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U16, out=None, syndromes=None,
+                 counts=None, cuda_stream=None):
+    """Decode a device tensor of shortened-code segments of length n.
+
+    Returns (out_words, syndromes or None, counts) where counts is an int64
+    tensor of two elements: [nonzero syndromes, syndromes past n]."""
+    import torch
+    r, k = hd_short_params(n)
+    dev = stream_words.device
+    if out is None:
+        out = torch.empty(max(4, words_for(num_codewords * k)), dtype=torch.int32, device=dev)
+    if syndromes is None and syn_type != SYN_NONE:
+        dt = torch.uint8 if syn_type == SYN_U8 else torch.int16
+        syndromes = torch.empty(max(16, num_codewords), dtype=dt, device=dev)
+    if counts is None:
+        counts = torch.empty(2, dtype=torch.int64, device=dev)
+    rc = hd_decode_short(_ptr(stream_words), n * num_codewords, n, num_codewords, _ptr(out),
+                         _ptr(syndromes) if syn_type != SYN_NONE else None, syn_type, _ptr(counts),
+                         _ptr(counts) + 8, _stream_handle(cuda_stream))
+    check(rc, "hd_decode_short")
+    return out, syndromes, counts
+
+
+def encode_short(data_words, n: int, num_codewords: int, out=None, cuda_stream=None):
+    """Encode a device tensor of packed messages into segments of length n."""
+    import torch
+    if out is None:
+        out = torch.empty(max(4, words_for(num_codewords * n)), dtype=torch.int32, device=data_words.device)
+    check(hd_encode_short(_ptr(data_words), n, num_codewords, _ptr(out), _stream_handle(cuda_stream)),
+          "hd_encode_short")
+    return out
 
 
 def encode(data_words, n: int, num_codewords: int, out=None, cuda_stream=None):

@@ -93,3 +93,50 @@ def test_host_decode_validation_host_only(lib):
     assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 15, 4, z.ctypes.data, None, 0, 128, 9)[0] == hd.HD_ERR_INVALID_ARG
     assert hd.hd_decode_host(None, 15 * 4, 15, 4, z.ctypes.data, None, 0, 0, 0)[0] == hd.HD_ERR_NULL
     assert hd.hd_decode_host(z.ctypes.data, 15 * 4, 15, 4, z.ctypes.data, None, 1, 0, 0)[0] == hd.HD_ERR_NULL
+
+
+def test_short_params_host_only(lib, oracle_mod):
+    for n in list(range(3, 600)) + [1611, 8013, 16383, 16384, 32767]:
+        assert hd.hd_short_params(n) == oracle_mod.short_params(n)
+    for bad in (0, 1, 2, 32768, 1 << 20):
+        with pytest.raises(hd.HDError):
+            hd.hd_short_params(bad)
+
+
+def test_segment_params_match_the_splitter_rule(lib, oracle_mod):
+    """Sec. II: a packet of M bytes cut into t segments; each segment carries
+    k = ceil(8M/t) data bits and the fewest checksum bits r with
+    2^r >= k + r + 1 (brute force here), so n = k + r is a shortened length."""
+    for M in list(range(1, 80)) + [400, 800, 1200, 1600, 2000, 4000]:
+        for t in range(1, 9):
+            if t > 8 * M:
+                continue
+            k = -(-8 * M // t)
+            r = next(r for r in range(1, 40) if 2 ** r >= k + r + 1)
+            if k + r < 3 or k + r > 32767:
+                continue
+            n, kk, rr = hd.hd_segment_params(M, t)
+            assert (n, kk, rr) == (k + r, k, r), (M, t)
+            assert oracle_mod.short_params(n) == (r, k)
+    assert lib.hd_segment_params(100, 0, None, None, None) == hd.HD_ERR_INVALID_ARG
+    assert lib.hd_segment_params(1, 9, None, None, None) == hd.HD_ERR_INVALID_ARG
+    assert lib.hd_segment_params(5000, 1, None, None, None) == hd.HD_ERR_SIZE
+
+
+def test_short_host_side_validation(lib):
+    assert hd.hd_decode_short(16, 2 * 4, 2, 4, 16, None, 0, None, None, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode_short(16, 32768, 32768, 1, 16, None, 0, None, None, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode_short(16, 11 * 4 + 1, 11, 4, 16, None, 0, None, None, None) == hd.HD_ERR_SIZE
+    assert hd.hd_decode_short(None, 11 * 4, 11, 4, 16, None, 0, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_short(16, 11 * 4, 11, 4, None, None, 0, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_short(16, 11 * 4, 11, 4, 16, None, hd.SYN_U16, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_short(20, 11 * 4, 11, 4, 16, None, 0, None, None, None) == hd.HD_ERR_ALIGN
+    assert hd.hd_decode_short(16, 11 * 4, 11, 4, 24, None, 0, None, None, None) == hd.HD_ERR_ALIGN
+    assert hd.hd_decode_short(16, 300 * 4, 300, 4, 16, 32, hd.SYN_U8, None, None, None) == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_short(16, 11 * 4, 11, 4, 16, 32, 5, None, None, None) == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_short(None, 0, 11, 0, None, None, 0, None, None, None) == hd.HD_OK
+    assert hd.hd_encode_short(16, 2, 4, 16, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_encode_short(None, 11, 4, 16, None) == hd.HD_ERR_NULL
+    assert hd.hd_encode_short(16, 11, 4, 20, None) == hd.HD_ERR_ALIGN
+    assert hd.hd_short_variant_count() >= 1
+    assert lib.hd_short_variant_select(hd.hd_short_variant_count()) == hd.HD_ERR_INVALID_ARG
