@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "hd_device.cuh"
 #include "hd_generic.cuh"
@@ -71,6 +72,7 @@ struct ShortArgs {
     uint32_t tlog;      // log2 of the team size of the syndrome pass
     int syn_type;
     float kinv;         // 1 / k, for the quotient estimate of the output pass
+    const uint32_t *table;  // output-word descriptors (see output_table)
 };
 
 template <int SB>
@@ -132,6 +134,19 @@ __device__ __forceinline__ uint32_t data_word(const uint32_t *st, uint32_t cb, u
     return v;
 }
 
+// Value of output word `wq` (global index) when it holds data bits of codeword
+// c (tile-relative) from data bit d on: a codeword's head (d < 26) or the
+// crossing into the next codeword (k - d < 32).  Returns the bits and the mask
+// of the bits this tile owns in the word.
+__device__ __forceinline__ uint32_t special_word(const uint32_t *st, const uint32_t *heads, uint32_t off0, uint32_t n,
+                                                 uint32_t k, uint32_t gcnt, uint32_t c, uint32_t d)
+{
+    uint32_t v = data_word(st, off0 + c * n, d, heads[c]);
+    const uint32_t rem = k - d;
+    if (rem < 32) v = (v & lowmask(rem)) | (c + 1 < gcnt ? heads[c + 1] << rem : 0u);
+    return v;
+}
+
 template <int W, int S, int SB>
 __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
 {
@@ -154,9 +169,11 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
     }
     __syncwarp();
 
-    const uint32_t T = 1u << a.tlog, tl = lane & (T - 1u), team = lane >> a.tlog, G = 32u >> a.tlog;
-    const uint32_t tmask = T == 32 ? 0xFFFFFFFFu : ((1u << T) - 1u) << (team * T);
-    const uint32_t n = a.n, k = a.k;
+    // syndrome teams: T lanes per codeword, G codewords per round
+    const uint32_t tlog = a.tlog, T = 1u << tlog, tl = lane & (T - 1u), team = lane >> tlog, G = 32u >> tlog;
+    const uint32_t n = a.n, k = a.k, Ym1 = a.Y - 1u;
+    const uint32_t tl_last = Ym1 & (T - 1u), i_last = Ym1 >> tlog;
+    const int32_t stage_bits = 8 * SB;  // reads past the data stay inside the stage's slack
     uint32_t errs = 0, dets = 0, it = 0;
     bool aborted = false;
     for (uint64_t t = gw; t < a.ntiles; t += tw, ++it) {
@@ -173,32 +190,62 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         tile_span(a, t, byte0, bytes, gcnt);
         const uint64_t c0 = t * a.g;
         const uint32_t off0 = (uint32_t)((c0 * n) & 127u);
-        // words past the last 16-byte boundary of the input arrive by plain loads
-        {
+        {  // words past the last 16-byte boundary of the input arrive by plain loads
             const uint64_t w0 = byte0 >> 2, wb = (byte0 + bytes) >> 2;
             const uint64_t we = min(((c0 + gcnt) * n + 31) >> 5, a.in_words);
-            for (uint64_t w = wb + lane; w < we; w += 32) st[w - w0] = a.in[w];
+            if (wb < we) {
+                for (uint64_t w = wb + lane; w < we; w += 32) st[w - w0] = a.in[w];
+                __syncwarp();
+            }
         }
-        __syncwarp();
 
-        // 1. syndromes: team `team` takes codeword cb + team, lane tl its words j = tl, tl + T, ...
+        // 1. syndromes.  Lane tl of a team reads position-domain words j = tl + T*i; the low
+        //    syndrome bits come from the XOR of all words, the high bits from the XOR of the
+        //    indices j of the odd-parity words: bit i of pm is the parity of word tl + T*i.
         for (uint32_t cbase = 0; cbase < gcnt; cbase += G) {
             const uint32_t c = cbase + team;
-            uint32_t x = 0, h = 0;
+            uint32_t x = 0, pm = 0;
             if (c < gcnt) {
-                const int32_t ybase = (int32_t)(off0 + c * n) - 1;  // stage bit of position 0
-                for (uint32_t j = tl; j < a.Y; j += T) {
-                    const int32_t q = ybase + 32 * (int32_t)j;
-                    const int32_t wi = q >> 5;  // -1 reads the guard word
-                    uint32_t w = __funnelshift_r(st[wi], st[wi + 1], (uint32_t)q & 31u);
-                    if (j == 0) w &= ~1u;
-                    if (j == a.Y - 1) w &= a.ylast;
-                    x ^= w;
-                    h ^= (__popc(w) & 1u) ? j : 0u;
+                const int32_t q0 = (int32_t)(off0 + c * n) - 1 + 32 * (int32_t)tl;  // position 0 is bit -1 of c
+                const uint32_t sh = (uint32_t)q0 & 31u;
+                int32_t wi = q0 >> 5;  // -1 reads the guard word
+                uint32_t cnt = tl < Ym1 ? (Ym1 - 1u - tl) / T + 1u : 0u;  // words before the last one
+                uint32_t lo = 0;  // only words of this codeword are read
+                if (T == 1) {  // one lane per codeword: each word is the next one's low half
+                    lo = st[wi];
+#pragma unroll 2
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const uint32_t hi = st[wi + 1];
+                        const uint32_t y = __funnelshift_r(lo, hi, sh);
+                        x ^= y;
+                        pm = (pm << 1) | (__popc(y) & 1u);  // bit order reversed below
+                        ++wi;
+                        lo = hi;
+                    }
+                } else {
+#pragma unroll 2
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const uint32_t y = __funnelshift_r(st[wi], st[wi + 1], sh);
+                        x ^= y;
+                        pm = (pm << 1) | (__popc(y) & 1u);
+                        wi += (int32_t)T;
+                    }
+                    if (tl == tl_last) lo = st[wi];
                 }
+                if (tl == tl_last) {  // the last word holds positions up to n only
+                    const uint32_t y = __funnelshift_r(lo, st[wi + 1], sh) & a.ylast;
+                    x ^= y;
+                    pm = (pm << 1) | (__popc(y) & 1u);
+                    ++cnt;
+                }
+                pm = cnt ? __brev(pm) >> (32u - cnt) : 0u;
             }
-            x = __reduce_xor_sync(tmask, x);
-            h = __reduce_xor_sync(tmask, h);
+            uint32_t h = ((__popc(pm) & 1u) ? tl : 0u) ^ (fold5(pm) << tlog);
+            // XOR over the team: butterfly steps stay inside aligned groups of T lanes
+            for (uint32_t o = T >> 1; o > 0; o >>= 1) {
+                x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                h ^= __shfl_xor_sync(0xFFFFFFFFu, h, o);
+            }
             if (tl == 0 && c < gcnt) {
                 const uint32_t syn = (h << 5) | fold5(x);
                 if (syn != 0) {
@@ -228,61 +275,71 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         }
         __syncwarp();
 
-        // 3. output words, four consecutive per lane (one 16-byte store when all are owned)
+        // 3. output words, lane-strided (conflict-free stage reads, coalesced stores).  The table
+        //    describes output word idx of a 32-codeword period (k words): the distance from bit
+        //    32*idx to the stage bit of the word's first data bit (counted from position 1 of the
+        //    period's first codeword) and how many data bits precede its one checksum position.
+        //    Words holding a codeword's head or a crossing are rewritten by pass 4.
         const uint64_t ob0 = c0 * k, ob1 = (c0 + gcnt) * k;
         const uint64_t F = ob0 >> 5, L = (ob1 - 1) >> 5;
-        const bool fs = (ob0 & 31u) != 0, ls = (ob1 & 31u) != 0 && (c0 + gcnt) < a.num_cw;
-        const uint64_t Fo = F + (fs ? 1 : 0), Lo = L - (ls ? 1 : 0);  // fully owned words
-        for (uint64_t qw = (F & ~3ull) + 4u * lane; qw <= L; qw += 128) {
-            uint32_t v[4];
-            // tile output bit of the quad's first word; words before the tile's first word
-            // are skipped and the tile's first word, if shared, holds only data bits of codeword 0
-            const int64_t e0 = (int64_t)(qw << 5) - (int64_t)ob0;
-            uint32_t c = 0, d = 0;
-            bool placed = false;
+        const bool fs = (ob0 & 31u) != 0, last_tile = (c0 + gcnt) == a.num_cw;
+        const bool ls = (ob1 & 31u) != 0 && !last_tile;
+        const int32_t nW = (int32_t)(L - F) + 1;                       // words of this tile
+        const int32_t wlo = fs ? 1 : 0, whi = nW - 1 - (ls ? 1 : 0);  // words it writes whole
+        {
+            // the table runs past one period, so a tile's words never wrap: word w of the tile is
+            // entry idxF + w, whose first data bit is at stage bit sb0 + 32 * (idxF + w) + delta
+            const uint32_t cr = (uint32_t)(c0 & 31u);
+            const int32_t idx0 = (int32_t)((cr * k) >> 5) + lane;
+            int32_t sbw = (int32_t)off0 - (int32_t)(cr * n) + 32 * idx0;
+            const uint32_t *tp = a.table + idx0;
+            uint32_t *outp = a.out + F + lane;
+            // four words per lane per iteration, 32 apart: their table loads are in flight
+            // together.  Words past the tile come from in-range entries and clamped stage
+            // bits and are never stored.
+            for (int32_t w0 = lane; w0 <= whi; w0 += 128, outp += 128, tp += 128, sbw += 4096) {
+                uint32_t e[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t e = e0 + 32 * u;
-                uint32_t val = 0;
-                if (e < 0) {
-                    if (e > -32) val = heads[0] << (uint32_t)(-e);
-                } else if (qw + u <= L) {
-                    if (!placed) {  // codeword and data bit of tile output bit e
-                        const uint32_t eu = (uint32_t)e;
-                        c = (uint32_t)((float)eu * a.kinv);
-                        if (c * k > eu) --c;
-                        if ((c + 1) * k <= eu) ++c;
-                        d = eu - c * k;
-                        placed = true;
-                    }
-                    const uint32_t cb = off0 + c * n;
-                    val = data_word(st, cb, d, heads[c]);
-                    const uint32_t rem = k - d;
-                    if (rem < 32) val = (val & lowmask(rem)) | (c + 1 < gcnt ? heads[c + 1] << rem : 0u);
-                    d += 32;
-                    if (d >= k) {
-                        d -= k;
-                        ++c;
-                    }
-                }
-                v[u] = val;
-            }
-            if (qw >= Fo && qw + 3 <= Lo) {
-                *reinterpret_cast<uint4 *>(a.out + qw) = make_uint4(v[0], v[1], v[2], v[3]);
-            } else {
+                for (int u = 0; u < 4; ++u) e[u] = __ldg(tp + 32 * u);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const uint64_t wq = qw + u;
-                    if (wq < F || wq > L) continue;
-                    if (wq >= Fo && wq <= Lo) {
-                        a.out[wq] = v[u];
-                    } else {
-                        // shared with the neighbouring tile: touch only this tile's bits
-                        const uint32_t own = (wq == F && fs) ? ~lowmask((uint32_t)(ob0 & 31u))
-                                                             : lowmask((uint32_t)(ob1 & 31u));
-                        atomicAnd(&a.out[wq], v[u] | ~own);
-                        atomicOr(&a.out[wq], v[u] & own);
-                    }
+                    const int32_t q = max(0, min(sbw + 1024 * u + (int32_t)(e[u] & 0xFFFFu), stage_bits));
+                    const uint32_t m = shl_clamp(1u, e[u] >> 16) - 1u;
+                    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1];
+                    const uint32_t sh = (uint32_t)q & 31u;
+                    const uint32_t v = (__funnelshift_r(lo, hi, sh) & m) | (__funnelshift_rc(lo, hi, sh + 1u) & ~m);
+                    const int32_t w = w0 + 32 * u;
+                    if (w >= wlo && w <= whi) outp[32 * u] = v;
+                }
+            }
+        }
+        const uint64_t Lo = ls ? L - 1 : L;
+        __syncwarp();  // orders pass 3's stores before pass 4 rewrites some of the same words
+
+        // 4. per codeword: the word where its data starts (crossing from the previous codeword,
+        //    or the tile's first word), the next word if it still holds head bits, and for the
+        //    last codeword the tile's last word
+        for (uint32_t c = lane; c < gcnt; c += 32) {
+            const uint64_t b = ob0 + (uint64_t)c * k;
+            const uint64_t ws = b >> 5;
+            const uint32_t al = (uint32_t)(b & 31u);
+            if (c == 0 && fs) {
+                const uint32_t own = ~lowmask(al), v = heads[0] << al;
+                atomicAnd(&a.out[ws], v | ~own);
+                atomicOr(&a.out[ws], v & own);
+            } else if (ws <= Lo) {
+                a.out[ws] = al == 0 ? heads[c] : special_word(st, heads, off0, n, k, gcnt, c - 1, k - al);
+            }
+            if (al > 6 && ws + 1 <= Lo) a.out[ws + 1] = special_word(st, heads, off0, n, k, gcnt, c, 32 - al);
+            if (c == gcnt - 1 && (ob1 & 31u) != 0) {
+                const uint32_t d = (uint32_t)((L << 5) - b);
+                const uint32_t v = special_word(st, heads, off0, n, k, gcnt, c, d);
+                if (ls) {
+                    const uint32_t own = lowmask((uint32_t)(ob1 & 31u));
+                    atomicAnd(&a.out[L], v | ~own);
+                    atomicOr(&a.out[L], v & own);
+                } else {
+                    a.out[L] = v;
                 }
             }
         }
@@ -502,18 +559,98 @@ int current_short_variant()
     return g_short_choice[dev] > 0 ? g_short_choice[dev] - 1 : 0;
 }
 
-uint32_t team_log(uint32_t Y)
+// Team size of the syndrome pass: a team of T lanes reads a codeword's Y
+// position-domain words, ceil(Y / T) per lane (at most 32: one bit each in the
+// parity mask), and pays a fixed cost per codeword for the reductions.  Pick
+// the T with the fewest lane instructions per tile by a simple cost model.
+uint32_t team_log(uint32_t Y, uint32_t g)
 {
-    // the team size (8, 16 or 32 lanes) that wastes the fewest lane slots; ties go to the larger team
-    uint32_t best = 5, best_slots = (Y + 31) / 32 * 32;
-    for (uint32_t lg = 4; lg >= 3; --lg) {
-        const uint32_t T = 1u << lg, slots = (Y + T - 1) / T * T;
-        if (slots < best_slots) {
+    uint32_t best = 5;
+    uint64_t best_cost = ~0ull;
+    for (uint32_t lg = 0; lg <= 5; ++lg) {
+        const uint32_t T = 1u << lg, G = 32u >> lg, per_lane = (Y + T - 1) / T;
+        if (per_lane > 32) continue;
+        const uint64_t cost = (uint64_t)((g + G - 1) / G) * 32u * (per_lane * 10u + 35u);
+        if (cost < best_cost) {
+            best_cost = cost;
             best = lg;
-            best_slots = slots;
         }
     }
     return best;
+}
+
+// Output-word descriptors: entry idx describes output word idx of a run of
+// codewords that starts at a multiple of 32 (32 codewords fill k words, so a
+// tile's first word is entry (c0 mod 32) * k / 32).  The table covers one
+// period of k words plus the longest tile and a lane's last group of reads,
+// so no tile wraps.  Entry = delta | split << 16: the word's first data bit
+// is at bit 32*idx + delta counted from position 1 of the run's first
+// codeword (delta = c*r + J + 1 for data bit d of codeword c in data run J),
+// and split data bits precede the word's checksum position (32 if none).
+// Words holding a codeword's first 26 data bits or crossing into the next
+// codeword are rewritten by the kernel's per-codeword pass; their entries only
+// point inside their codeword.
+std::vector<uint32_t> output_table(uint32_t n, uint32_t k, uint32_t max_tile_words)
+{
+    const uint32_t r = n - k;
+    const uint32_t len = k + max_tile_words + 128;
+    std::vector<uint32_t> t(len, 0);
+    for (uint32_t idx = 0; idx < len; ++idx) {
+        const uint64_t e = 32ull * idx;
+        const uint32_t c = (uint32_t)(e / k), d = (uint32_t)(e % k);
+        uint32_t delta = c * r + 1u, split = 32;
+        if (d >= 26 && k - d >= 32) {
+            uint32_t J = 5;
+            while (d >= (2u << J) - J - 2u) ++J;  // data run J holds data bits 2^J - J - 1 .. 2^(J+1) - J - 3
+            delta = c * r + J + 1u;
+            split = std::min<uint32_t>(32u, (2u << J) - J - 2u - d);
+        }
+        t[idx] = delta | (split << 16);
+    }
+    return t;
+}
+
+struct TableEntry {
+    uint32_t n = 0;
+    uint32_t *dev = nullptr;
+    uint64_t used = 0;
+};
+constexpr int kMaxTables = 32;
+TableEntry g_tables[64][kMaxTables];
+uint64_t g_table_clock = 0;
+
+// The descriptor table of length n on the current device, built on first use.
+const uint32_t *table_for(uint32_t n, uint32_t k)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    TableEntry *slot = nullptr;
+    for (TableEntry &e : g_tables[dev]) {
+        if (e.n == n && e.dev) {
+            e.used = ++g_table_clock;
+            return e.dev;
+        }
+        if (!slot || (!e.dev && slot->dev) || (e.dev && slot->dev && e.used < slot->used)) slot = &e;
+    }
+    if (slot->dev) {  // evict the least recently used table once no kernel can still read it
+        if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+        cudaFree(slot->dev);
+        slot->dev = nullptr;
+    }
+    // the longest tile of any configuration: the largest stage's codewords, plus a partial word
+    const uint32_t max_words = (uint32_t)(((uint64_t)tile_codewords<8192>(n) * k + 31) / 32) + 1;
+    const std::vector<uint32_t> host = output_table(n, k, max_words);
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, host.size() * 4) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    slot->n = n;
+    slot->dev = d;
+    slot->used = ++g_table_clock;
+    return d;
 }
 
 cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
@@ -546,7 +683,9 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     a.Y = (n + 32) / 32;
     const uint32_t lastbits = n + 1 - 32 * (a.Y - 1);
     a.ylast = lastbits >= 32 ? 0xFFFFFFFFu : (1u << lastbits) - 1u;
-    a.tlog = team_log(a.Y);
+    a.tlog = team_log(a.Y, a.g);
+    a.table = table_for(n, k);
+    if (!a.table) return cudaErrorMemoryAllocation;
     a.syn_type = syn ? syn_type : 0;
     a.kinv = 1.0f / (float)k;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
