@@ -12,12 +12,15 @@
 // Two decoders:
 //  * k_short_tiles (k >= 64, i.e. n >= 71): each warp streams tiles of g whole
 //    codewords through a ring of shared-memory stages filled by 1-D bulk
-//    copies.  Per tile it computes the syndromes (teams of T lanes per
-//    codeword, one redux per team), applies the corrections in the stage,
-//    then builds the output words directly: every 32-bit output word is at
-//    most two runs of one codeword's stage bits (the runs between checksum
-//    positions are at least 31 bits long past data bit 26), plus the
-//    codeword's first 32 data bits taken from a per-codeword head word.
+//    copies.  Per tile: (1) syndromes, teams of T lanes per codeword (T from a
+//    cost model, 1..32), each lane folding its position-domain words into an
+//    XOR and a parity mask, then a butterfly over the team; the corrections
+//    flip bits in the stage.  (3) Every output word from a per-length table of
+//    output-word offsets: a funnel shift (and, for short codewords, a merge at
+//    the word's checksum position), lane-strided so stage reads are
+//    conflict-free and stores coalesced.  (4) The words that hold a codeword's
+//    first 26 data bits or cross into the next codeword, per codeword.  (5) For
+//    long codewords, the few words that hold a checksum position.
 //  * k_short_small (n <= 255): warp tiles of 32 codewords straight from global
 //    memory, one codeword per lane, like the generic full-length kernel.
 // The encoder (k_encode_short) is bit-serial, one thread per codeword: it is
@@ -25,6 +28,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "hd_device.cuh"
@@ -71,8 +75,10 @@ struct ShortArgs {
     uint32_t ylast;     // valid-bit mask of the last position-domain word
     uint32_t tlog;      // log2 of the team size of the syndrome pass
     int syn_type;
-    float kinv;         // 1 / k, for the quotient estimate of the output pass
-    const uint32_t *table;  // output-word descriptors (see output_table)
+    const void *table;      // output-word offsets (see output_table), tab_len entries of 2 or 4 bytes
+    uint32_t tab_len;
+    uint32_t nJ;            // data runs J >= 5 that end inside the codeword's data (D_J < k)
+    uint32_t nJ_magic;      // ceil(2^32 / nJ) for nJ > 1: f / nJ = umulhi(f, nJ_magic) for the small f used
 };
 
 template <int SB>
@@ -113,50 +119,66 @@ __device__ __forceinline__ void issue_tile(const ShortArgs &a, uint64_t t, uint8
     if (bytes) bulk_g2s(stage + 16, reinterpret_cast<const uint8_t *>(a.in) + byte0, bytes, bar);
 }
 
-// 32 data bits of codeword c starting at data bit d (d + 32 <= k, d >= 26 or
-// taken through the head word).  cb: stage bit of position 1 of codeword c.
-__device__ __forceinline__ uint32_t data_word(const uint32_t *st, uint32_t cb, uint32_t d, uint32_t head_c)
+// 32-bit loads from a shared-memory byte address (and the word after it).
+__device__ __forceinline__ uint32_t lds32(uint32_t addr)
 {
-    const bool head = d < 26;
-    const uint32_t dx = head ? 32u : d;
-    // dx lies in data run J: positions 2^J + 1 .. 2^(J+1) - 1, data bit dx at position dx + J + 2
-    const uint32_t J1 = 31u - __clz(dx);
-    const uint32_t J = J1 + ((dx + J1 + 2u) >> (J1 + 1u));
-    const uint32_t q = cb + dx + J + 1u;
-    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1];
-    const uint32_t sh = q & 31u;
-    const uint32_t a = __funnelshift_r(lo, hi, sh);
-    const uint32_t b = __funnelshift_rc(lo, hi, sh + 1u);  // skips the checksum position 2^(J+1)
-    const uint32_t r1 = (2u << J) - J - 2u - dx;            // data bits before that position
-    const uint32_t lm = lowmask(r1);
-    uint32_t v = (a & lm) | (b & ~lm);
-    if (head) v = d == 0 ? head_c : (head_c >> d) | (v << (32u - d));
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
 
-// Value of output word `wq` (global index) when it holds data bits of codeword
-// c (tile-relative) from data bit d on: a codeword's head (d < 26) or the
-// crossing into the next codeword (k - d < 32).  Returns the bits and the mask
-// of the bits this tile owns in the word.
-__device__ __forceinline__ uint32_t special_word(const uint32_t *st, const uint32_t *heads, uint32_t off0, uint32_t n,
-                                                 uint32_t k, uint32_t gcnt, uint32_t c, uint32_t d)
+__device__ __forceinline__ uint32_t lds32_next(uint32_t addr)
 {
-    uint32_t v = data_word(st, off0 + c * n, d, heads[c]);
-    const uint32_t rem = k - d;
-    if (rem < 32) v = (v & lowmask(rem)) | (c + 1 < gcnt ? heads[c + 1] << rem : 0u);
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+4];" : "=r"(v) : "r"(addr));
     return v;
 }
 
-template <int W, int S, int SB>
+// The first 32 data bits of the codeword whose position 1 is stage bit cb
+// (positions 3, 5-7, 9-15, 17-31, 33-38).
+__device__ __forceinline__ uint32_t head_word(const uint32_t *st, uint32_t cb)
+{
+    const int32_t q = (int32_t)cb - 1;
+    const int32_t wi = q >> 5;  // -1 reads the guard word
+    const uint32_t sh = (uint32_t)q & 31u;
+    const uint32_t y0 = __funnelshift_r(st[wi], st[wi + 1], sh);
+    const uint32_t y1 = __funnelshift_r(st[wi + 1], st[wi + 2], sh);
+    return ((y0 >> 3) & 1u) | ((y0 >> 4) & 0xEu) | ((y0 >> 5) & 0x7F0u) | ((y0 >> 6) & 0x3FFF800u) |
+           ((y1 << 25) & 0xFC000000u);
+}
+
+// 32 data bits of the codeword whose position 1 is stage bit cb, from data bit
+// d >= 26 on (so at most one checksum position falls inside).
+__device__ __forceinline__ uint32_t run_word(const uint32_t *st, uint32_t cb, uint32_t d)
+{
+    const uint32_t J1 = 31u - __clz(d);
+    const uint32_t J = J1 + ((d + J1 + 2u) >> (J1 + 1u));  // data run of bit d
+    const uint32_t q = cb + d + J + 1u;
+    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1], sh = q & 31u;
+    const uint32_t m = lowmask((2u << J) - J - 2u - d);
+    return (__funnelshift_r(lo, hi, sh) & m) | (__funnelshift_rc(lo, hi, sh + 1u) & ~m);
+}
+
+template <int W, int S, int SB, bool TAB_SMEM, bool SPLIT>
 __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
 {
     using Geom = TileGeom<SB>;
     extern __shared__ __align__(128) uint8_t smem[];
-    constexpr uint32_t warp_bytes = S * Geom::stage_stride + Geom::max_g * 4 + 16 * S;
+    constexpr uint32_t warp_bytes = S * Geom::stage_stride + 16 * S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the output-word table, copied once per CTA when it fits next to the stages
+    // SPLIT: 32-bit entries that also say where a word's checksum position falls, resolved
+    // in pass 3; otherwise 16-bit entries and pass 5 rewrites those words
+    using Entry = typename std::conditional<SPLIT, uint32_t, uint16_t>::type;
+    const Entry *tab = static_cast<const Entry *>(a.table);
+    if constexpr (TAB_SMEM) {
+        Entry *s_tab = reinterpret_cast<Entry *>(smem + W * warp_bytes);
+        for (uint32_t i = threadIdx.x; i < a.tab_len; i += W * 32) s_tab[i] = tab[i];
+        __syncthreads();
+        tab = s_tab;
+    }
     uint8_t *wbase = smem + warp * warp_bytes;
-    uint32_t *heads = reinterpret_cast<uint32_t *>(wbase + S * Geom::stage_stride);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + S * Geom::stage_stride + Geom::max_g * 4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + S * Geom::stage_stride);
     const uint64_t gw = (uint64_t)blockIdx.x * W + warp, tw = (uint64_t)gridDim.x * W;
 
     if (lane == 0) {
@@ -172,7 +194,7 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
     // syndrome teams: T lanes per codeword, G codewords per round
     const uint32_t tlog = a.tlog, T = 1u << tlog, tl = lane & (T - 1u), team = lane >> tlog, G = 32u >> tlog;
     const uint32_t n = a.n, k = a.k, Ym1 = a.Y - 1u;
-    const uint32_t tl_last = Ym1 & (T - 1u), i_last = Ym1 >> tlog;
+    const uint32_t tl_last = Ym1 & (T - 1u);
     const int32_t stage_bits = 8 * SB;  // reads past the data stay inside the stage's slack
     uint32_t errs = 0, dets = 0, it = 0;
     bool aborted = false;
@@ -185,6 +207,7 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         }
         uint8_t *stage = wbase + s * Geom::stage_stride;
         uint32_t *st = reinterpret_cast<uint32_t *>(stage + 16);
+        const uint32_t st_s = smem_addr(st);
         uint64_t byte0;
         uint32_t bytes, gcnt;
         tile_span(a, t, byte0, bytes, gcnt);
@@ -211,29 +234,31 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
                 int32_t wi = q0 >> 5;  // -1 reads the guard word
                 uint32_t cnt = tl < Ym1 ? (Ym1 - 1u - tl) / T + 1u : 0u;  // words before the last one
                 uint32_t lo = 0;  // only words of this codeword are read
+                uint32_t ad = st_s + (uint32_t)(wi * 4);
                 if (T == 1) {  // one lane per codeword: each word is the next one's low half
-                    lo = st[wi];
-#pragma unroll 2
+                    lo = lds32(ad);
+#pragma unroll 4
                     for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t hi = st[wi + 1];
+                        const uint32_t hi = lds32_next(ad);
+                        ad += 4;
                         const uint32_t y = __funnelshift_r(lo, hi, sh);
                         x ^= y;
                         pm = (pm << 1) | (__popc(y) & 1u);  // bit order reversed below
-                        ++wi;
                         lo = hi;
                     }
                 } else {
-#pragma unroll 2
+                    const uint32_t step = 4u * T;
+#pragma unroll 4
                     for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t y = __funnelshift_r(st[wi], st[wi + 1], sh);
+                        const uint32_t y = __funnelshift_r(lds32(ad), lds32_next(ad), sh);
                         x ^= y;
                         pm = (pm << 1) | (__popc(y) & 1u);
-                        wi += (int32_t)T;
+                        ad += step;
                     }
-                    if (tl == tl_last) lo = st[wi];
+                    if (tl == tl_last) lo = lds32(ad);
                 }
                 if (tl == tl_last) {  // the last word holds positions up to n only
-                    const uint32_t y = __funnelshift_r(lo, st[wi + 1], sh) & a.ylast;
+                    const uint32_t y = __funnelshift_r(lo, lds32_next(ad), sh) & a.ylast;
                     x ^= y;
                     pm = (pm << 1) | (__popc(y) & 1u);
                     ++cnt;
@@ -263,18 +288,6 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         }
         __syncwarp();
 
-        // 2. head words: data bits 0..31 of each codeword (positions 3, 5-7, 9-15, 17-31, 33-38)
-        for (uint32_t c = lane; c < gcnt; c += 32) {
-            const int32_t q = (int32_t)(off0 + c * n) - 1;
-            const int32_t wi = q >> 5;
-            const uint32_t sh = (uint32_t)q & 31u;
-            const uint32_t y0 = __funnelshift_r(st[wi], st[wi + 1], sh);
-            const uint32_t y1 = __funnelshift_r(st[wi + 1], st[wi + 2], sh);
-            heads[c] = ((y0 >> 3) & 1u) | ((y0 >> 4) & 0xEu) | ((y0 >> 5) & 0x7F0u) | ((y0 >> 6) & 0x3FFF800u) |
-                       ((y1 << 25) & 0xFC000000u);
-        }
-        __syncwarp();
-
         // 3. output words, lane-strided (conflict-free stage reads, coalesced stores).  The table
         //    describes output word idx of a 32-codeword period (k words): the distance from bit
         //    32*idx to the stage bit of the word's first data bit (counted from position 1 of the
@@ -292,56 +305,76 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
             const uint32_t cr = (uint32_t)(c0 & 31u);
             const int32_t idx0 = (int32_t)((cr * k) >> 5) + lane;
             int32_t sbw = (int32_t)off0 - (int32_t)(cr * n) + 32 * idx0;
-            const uint32_t *tp = a.table + idx0;
+            const Entry *tp = tab + idx0;
             uint32_t *outp = a.out + F + lane;
-            // four words per lane per iteration, 32 apart: their table loads are in flight
-            // together.  Words past the tile come from in-range entries and clamped stage
-            // bits and are never stored.
+            // four words per lane per iteration, 32 apart.  Words past the tile come from
+            // in-range entries and clamped stage bits and are never stored.
             for (int32_t w0 = lane; w0 <= whi; w0 += 128, outp += 128, tp += 128, sbw += 4096) {
                 uint32_t e[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) e[u] = __ldg(tp + 32 * u);
+                for (int u = 0; u < 4; ++u) e[u] = tp[32 * u];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int32_t q = max(0, min(sbw + 1024 * u + (int32_t)(e[u] & 0xFFFFu), stage_bits));
-                    const uint32_t m = shl_clamp(1u, e[u] >> 16) - 1u;
-                    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1];
-                    const uint32_t sh = (uint32_t)q & 31u;
-                    const uint32_t v = (__funnelshift_r(lo, hi, sh) & m) | (__funnelshift_rc(lo, hi, sh + 1u) & ~m);
+                    const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1], sh = (uint32_t)q & 31u;
+                    uint32_t v = __funnelshift_r(lo, hi, sh);
+                    if constexpr (SPLIT) {
+                        const uint32_t m = shl_clamp(1u, e[u] >> 16) - 1u;
+                        v = (v & m) | (__funnelshift_rc(lo, hi, sh + 1u) & ~m);
+                    }
                     const int32_t w = w0 + 32 * u;
                     if (w >= wlo && w <= whi) outp[32 * u] = v;
                 }
             }
         }
-        const uint64_t Lo = ls ? L - 1 : L;
         __syncwarp();  // orders pass 3's stores before pass 4 rewrites some of the same words
 
         // 4. per codeword: the word where its data starts (crossing from the previous codeword,
         //    or the tile's first word), the next word if it still holds head bits, and for the
-        //    last codeword the tile's last word
+        //    last codeword the tile's last word.  Word indices are tile-relative.
         for (uint32_t c = lane; c < gcnt; c += 32) {
-            const uint64_t b = ob0 + (uint64_t)c * k;
-            const uint64_t ws = b >> 5;
-            const uint32_t al = (uint32_t)(b & 31u);
+            const uint32_t b = (uint32_t)(ob0 & 31u) + c * k;  // tile bit of the codeword's data bit 0
+            const int32_t ws = (int32_t)(b >> 5);
+            const uint32_t al = b & 31u;
+            const uint32_t cb = off0 + c * n;  // stage bit of position 1
+            const uint32_t head = head_word(st, cb);
+            uint32_t *o = a.out + F + ws;
             if (c == 0 && fs) {
-                const uint32_t own = ~lowmask(al), v = heads[0] << al;
-                atomicAnd(&a.out[ws], v | ~own);
-                atomicOr(&a.out[ws], v & own);
-            } else if (ws <= Lo) {
-                a.out[ws] = al == 0 ? heads[c] : special_word(st, heads, off0, n, k, gcnt, c - 1, k - al);
+                const uint32_t own = ~lowmask(al), v = head << al;
+                atomicAnd(o, v | ~own);
+                atomicOr(o, v & own);
+            } else if (ws <= whi) {
+                *o = al == 0 ? head : (run_word(st, cb - n, k - al) & lowmask(al)) | (head << al);
             }
-            if (al > 6 && ws + 1 <= Lo) a.out[ws + 1] = special_word(st, heads, off0, n, k, gcnt, c, 32 - al);
+            if (al > 6 && ws + 1 <= whi) {
+                // data bits 32 - al .. 63 - al: the head word's top bits, then data bits 32.. (positions
+                // 39..63 of run 5, then run 6 after position 64)
+                const uint32_t q = cb + 38u;
+                const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1], sh = q & 31u;
+                const uint32_t x2 = (__funnelshift_r(lo, hi, sh) & 0x1FFFFFFu) |
+                                    (__funnelshift_rc(lo, hi, sh + 1u) & ~0x1FFFFFFu);
+                o[1] = (head >> (32u - al)) | (x2 << al);
+            }
             if (c == gcnt - 1 && (ob1 & 31u) != 0) {
-                const uint32_t d = (uint32_t)((L << 5) - b);
-                const uint32_t v = special_word(st, heads, off0, n, k, gcnt, c, d);
+                const uint32_t rem = (uint32_t)(ob1 & 31u);
+                const uint32_t v = run_word(st, cb, k - rem) & lowmask(rem);
+                uint32_t *ol = a.out + L;
                 if (ls) {
-                    const uint32_t own = lowmask((uint32_t)(ob1 & 31u));
-                    atomicAnd(&a.out[L], v | ~own);
-                    atomicOr(&a.out[L], v & own);
+                    atomicAnd(ol, v | ~lowmask(rem));
+                    atomicOr(ol, v);
                 } else {
-                    a.out[L] = v;
+                    *ol = v;
                 }
             }
+        }
+        // 5. words with a checksum position inside (data run J ends at data bit D_J = 2^(J+1) - J - 2,
+        //    J >= 5): pass 3 read them with one shift; lanes take (codeword, J) pairs
+        for (uint32_t f = lane; !SPLIT && f < gcnt * a.nJ; f += 32) {
+            const uint32_t c = a.nJ == 1 ? f : __umulhi(f, a.nJ_magic), J = 5u + (f - c * a.nJ);
+            const uint32_t b0 = (uint32_t)(ob0 & 31u) + c * k;   // tile bit of the codeword's data bit 0
+            const uint32_t bd = b0 + (2u << J) - J - 2u;          // tile bit of data bit D_J
+            const uint32_t dw = (bd & ~31u) - b0;                 // data bit at the start of its word (>= 26)
+            if ((bd & 31u) != 0 && dw + 32u <= k) a.out[F + (bd >> 5)] = run_word(st, off0 + c * n, dw);
         }
         // the corrections wrote the stage through the generic proxy; the refill writes it through the async one
         fence_proxy_async_smem();
@@ -498,56 +531,78 @@ __global__ void k_encode_short(const uint32_t *__restrict__ data, uint64_t data_
 // ---------------------------------------------------------------------------
 struct ShortVariant {
     int W, S, SB;
-    uint32_t smem;
-    const void *kernel;
-    void (*launch)(const ShortArgs &, int grid, cudaStream_t);
+    uint32_t stage_smem;  // dynamic shared memory of the warps' stages
+    // [0]: table in global memory; [1]: table in shared memory; [2]: shared, splits in pass 3
+    const void *kernel[3];
+    void (*launch[3])(const ShortArgs &, int grid, uint32_t smem, cudaStream_t);
 };
 
-template <int W, int S, int SB>
-void launch_tiles(const ShortArgs &a, int grid, cudaStream_t st)
+template <int W, int S, int SB, bool TAB_SMEM, bool SPLIT>
+void launch_tiles(const ShortArgs &a, int grid, uint32_t smem, cudaStream_t st)
 {
-    constexpr uint32_t warp_bytes = S * TileGeom<SB>::stage_stride + TileGeom<SB>::max_g * 4 + 16 * S;
-    k_short_tiles<W, S, SB><<<grid, W * 32, W * warp_bytes, st>>>(a);
+    k_short_tiles<W, S, SB, TAB_SMEM, SPLIT><<<grid, W * 32, smem, st>>>(a);
 }
 
 template <int W, int S, int SB>
 ShortVariant make_short_variant()
 {
-    constexpr uint32_t warp_bytes = S * TileGeom<SB>::stage_stride + TileGeom<SB>::max_g * 4 + 16 * S;
-    return ShortVariant{W, S, SB, W * warp_bytes, reinterpret_cast<const void *>(k_short_tiles<W, S, SB>),
-                        &launch_tiles<W, S, SB>};
+    constexpr uint32_t warp_bytes = S * TileGeom<SB>::stage_stride + 16 * S;
+    return ShortVariant{W,
+                        S,
+                        SB,
+                        W * warp_bytes,
+                        {reinterpret_cast<const void *>(k_short_tiles<W, S, SB, false, false>),
+                         reinterpret_cast<const void *>(k_short_tiles<W, S, SB, true, false>),
+                         reinterpret_cast<const void *>(k_short_tiles<W, S, SB, true, true>)},
+                        {&launch_tiles<W, S, SB, false, false>, &launch_tiles<W, S, SB, true, false>,
+                         &launch_tiles<W, S, SB, true, true>}};
 }
 
 const ShortVariant kShortVariants[] = {
+    make_short_variant<8, 2, 4096>(),  // the built-in choice: fastest over the paper's (M, t) grid on GB300
     make_short_variant<4, 2, 8192>(),
     make_short_variant<4, 3, 4096>(),
-    make_short_variant<8, 2, 4096>(),
     make_short_variant<4, 4, 2048>(),
 };
 constexpr int kNumShortVariants = sizeof(kShortVariants) / sizeof(kShortVariants[0]);
+constexpr uint32_t kTabSmemMax = 40u << 10;  // larger tables stay in global memory
 
 std::mutex g_short_mu;
-int g_short_bps[64][kNumShortVariants];  // resident CTAs per SM, 0 = not configured
-int g_short_choice[64] = {};             // selected variant per device (index + 1; 0 = default)
+int g_short_choice[64] = {};  // selected variant per device (index + 1; 0 = default)
 
-int short_blocks_per_sm(int v)
+struct OccEntry {
+    int v = -1, tsm = 0;
+    uint32_t smem = 0;
+    int bps = 0;
+};
+OccEntry g_occ[64][32];
+
+// Resident CTAs per SM of configuration v with `smem` bytes of dynamic shared memory.
+int short_blocks_per_sm(int v, int tsm, uint32_t smem)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
     std::lock_guard<std::mutex> lk(g_short_mu);
-    if (g_short_bps[dev][v] == 0) {
-        const ShortVariant &sv = kShortVariants[v];
-        if (cudaFuncSetAttribute(sv.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv.smem) !=
-            cudaSuccess)
-            return -1;
-        int bps = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sv.kernel, sv.W * 32, sv.smem) != cudaSuccess ||
-            bps <= 0)
-            return -1;
-        g_short_bps[dev][v] = bps;
-    }
-    return g_short_bps[dev][v];
+    for (const OccEntry &e : g_occ[dev])
+        if (e.v == v && e.tsm == tsm && e.smem == smem) return e.bps;
+    const ShortVariant &sv = kShortVariants[v];
+    // the attribute is per kernel: allow the device's largest opt-in size once, never a smaller one
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        (uint32_t)optin < smem ||
+        cudaFuncSetAttribute(sv.kernel[tsm], cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        return -1;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sv.kernel[tsm], sv.W * 32, smem) != cudaSuccess ||
+        bps <= 0)
+        return -1;
+    for (OccEntry &e : g_occ[dev])
+        if (e.v < 0) {
+            e = OccEntry{v, tsm, smem, bps};
+            break;
+        }
+    return bps;
 }
 
 int current_short_variant()
@@ -579,17 +634,16 @@ uint32_t team_log(uint32_t Y, uint32_t g)
     return best;
 }
 
-// Output-word descriptors: entry idx describes output word idx of a run of
+// Output-word offsets: entry idx describes output word idx of a run of
 // codewords that starts at a multiple of 32 (32 codewords fill k words, so a
 // tile's first word is entry (c0 mod 32) * k / 32).  The table covers one
 // period of k words plus the longest tile and a lane's last group of reads,
-// so no tile wraps.  Entry = delta | split << 16: the word's first data bit
-// is at bit 32*idx + delta counted from position 1 of the run's first
-// codeword (delta = c*r + J + 1 for data bit d of codeword c in data run J),
-// and split data bits precede the word's checksum position (32 if none).
-// Words holding a codeword's first 26 data bits or crossing into the next
-// codeword are rewritten by the kernel's per-codeword pass; their entries only
-// point inside their codeword.
+// so no tile wraps.  Entry = delta: the word's first data bit is at bit
+// 32*idx + delta counted from position 1 of the run's first codeword
+// (delta = c*r + J + 1 for data bit d of codeword c in data run J).  Words
+// holding a codeword's first 26 data bits, crossing into the next codeword or
+// holding a checksum position are rewritten by the kernel's per-codeword
+// passes; the first two kinds only point inside their codeword.
 std::vector<uint32_t> output_table(uint32_t n, uint32_t k, uint32_t max_tile_words)
 {
     const uint32_t r = n - k;
@@ -610,17 +664,24 @@ std::vector<uint32_t> output_table(uint32_t n, uint32_t k, uint32_t max_tile_wor
     return t;
 }
 
+// Where the words holding a checksum position are resolved: per word in the
+// output pass (32-bit entries) when k is small, so that codewords have few
+// words and such words are common; else in a per-codeword pass (16-bit
+// entries, half the table).
+bool split_in_pass3(uint32_t k) { return k < 1280; }
+
 struct TableEntry {
     uint32_t n = 0;
-    uint32_t *dev = nullptr;
+    void *dev = nullptr;
+    uint32_t len = 0;
     uint64_t used = 0;
 };
 constexpr int kMaxTables = 32;
 TableEntry g_tables[64][kMaxTables];
 uint64_t g_table_clock = 0;
 
-// The descriptor table of length n on the current device, built on first use.
-const uint32_t *table_for(uint32_t n, uint32_t k)
+// The output-word table of length n on the current device, built on first use.
+const void *table_for(uint32_t n, uint32_t k, uint32_t *len)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
@@ -629,6 +690,7 @@ const uint32_t *table_for(uint32_t n, uint32_t k)
     for (TableEntry &e : g_tables[dev]) {
         if (e.n == n && e.dev) {
             e.used = ++g_table_clock;
+            *len = e.len;
             return e.dev;
         }
         if (!slot || (!e.dev && slot->dev) || (e.dev && slot->dev && e.used < slot->used)) slot = &e;
@@ -640,16 +702,24 @@ const uint32_t *table_for(uint32_t n, uint32_t k)
     }
     // the longest tile of any configuration: the largest stage's codewords, plus a partial word
     const uint32_t max_words = (uint32_t)(((uint64_t)tile_codewords<8192>(n) * k + 31) / 32) + 1;
-    const std::vector<uint32_t> host = output_table(n, k, max_words);
-    uint32_t *d = nullptr;
-    if (cudaMalloc(&d, host.size() * 4) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    const std::vector<uint32_t> full = output_table(n, k, max_words);
+    const bool wide = split_in_pass3(k);
+    std::vector<uint16_t> narrow;
+    if (!wide)
+        for (uint32_t e : full) narrow.push_back((uint16_t)(e & 0xFFFFu));
+    const size_t bytes = wide ? full.size() * 4 : narrow.size() * 2;
+    const void *src = wide ? static_cast<const void *>(full.data()) : static_cast<const void *>(narrow.data());
+    void *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(d);
         return nullptr;
     }
     slot->n = n;
     slot->dev = d;
+    slot->len = (uint32_t)full.size();
     slot->used = ++g_table_clock;
+    *len = slot->len;
     return d;
 }
 
@@ -657,8 +727,6 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
                                int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st)
 {
     const ShortVariant &v = kShortVariants[vi];
-    const int bps = short_blocks_per_sm(vi);
-    if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint32_t r = short_r(n), k = n - r;
     ShortArgs a{};
     a.in = in;
@@ -684,14 +752,23 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     const uint32_t lastbits = n + 1 - 32 * (a.Y - 1);
     a.ylast = lastbits >= 32 ? 0xFFFFFFFFu : (1u << lastbits) - 1u;
     a.tlog = team_log(a.Y, a.g);
-    a.table = table_for(n, k);
+    a.table = table_for(n, k, &a.tab_len);
     if (!a.table) return cudaErrorMemoryAllocation;
     a.syn_type = syn ? syn_type : 0;
-    a.kinv = 1.0f / (float)k;
+    a.nJ = 0;
+    for (uint32_t J = 5; (2u << J) - J - 2u < k; ++J) ++a.nJ;
+    a.nJ_magic = a.nJ > 1 ? (uint32_t)((0x100000000ull + a.nJ - 1) / a.nJ) : 0u;
+    const bool split = split_in_pass3(k);
+    const uint32_t tab_bytes = (a.tab_len * (split ? 4u : 2u) + 15) & ~15u;
+    const int tsm = split ? 2 : (tab_bytes <= kTabSmemMax ? 1 : 0);  // split tables are small
+    const uint32_t smem = v.stage_smem + (tsm ? tab_bytes : 0u);
+    if (split) a.nJ = 0;  // no per-codeword pass for checksum words
+    const int bps = short_blocks_per_sm(vi, tsm, smem);
+    if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (a.ntiles + v.W - 1) / v.W;
     const int grid = (int)std::min(want, cap);
-    v.launch(a, grid, st);
+    v.launch[tsm](a, grid, smem, st);
     count_launch();
     return cudaGetLastError();
 }
@@ -753,7 +830,7 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
     const int syn = syndromes ? (int)syn_type : 0;
     if (k >= kLongMinK) {
         int vi = current_short_variant();
-        if (kShortVariants[vi].SB * 8u < n + 256u) vi = 0;  // stage too small for one codeword: largest stage
+        if (kShortVariants[vi].SB * 8u < n + 256u) vi = 1;  // stage too small for one codeword: largest stage
         if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
                                st) != cudaSuccess)
             return HD_ERR_CUDA;

@@ -202,3 +202,10 @@ def test_paper_grid_full_size_sampled(M, t):
         assert np.array_equal(_bits_of(outh, int(i) * k, k), want[j]), f"segment {i}"
     assert np.array_equal(synh[pick], es)
     assert hd.hd_device_status() == 0
+
+
+def test_alternating_lengths():
+    # the shared-memory need of the tiled kernel depends on n; a long length after a
+    # shorter one must still launch (and give the same bits)
+    for n in (8013, 300, 4096, 8013, 71, 32767, 545):
+        _check(n, 97 if n < 10000 else 9, hd.SYN_U16, seed=n + 31)
