@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-packets", type=int, default=100000)
     ap.add_argument("--serve-rates", type=str, default="1e4,1e5,1e6", help="Poisson arrival rates, packets/s")
+    ap.add_argument("--no-shortened", action="store_true", help="skip the shortened-code (M, t) grid section")
+    ap.add_argument("--shortened-only", action="store_true", help="run only the shortened-code section")
+    ap.add_argument("--short-steps", type=int, default=10, help="timed launches per (M, t) configuration")
     return ap.parse_args()
 
 
@@ -413,6 +416,85 @@ def run_batched(dev, args, peak, keep_pool=False):
     return res
 
 
+# The paper's evaluation grid (Sec. IV-A): packets of M bytes cut into t
+# segments, each a shortened Hamming codeword (hd_segment_params).
+SHORT_GRID = [(M, t) for M in (400, 800, 1200, 1600, 2000) for t in (2, 3, 4, 5, 6)]
+SHORT_INPUT_BYTES = 256 << 20  # per configuration: larger than L2, so every launch streams from HBM
+SHORT_P1, SHORT_P2 = 0.05, 0.005
+
+
+def run_shortened(dev, args, peak):
+    """Decode throughput over the paper's (M, t) grid: for each configuration
+    ~256 MB of packets, all t segments of all packets in one hd_decode_short
+    launch (u16 syndromes, both counters), after hd_short_autotune for that
+    segment length.  The bit-by-bit oracle decodes 64 packets on one host
+    thread for the speedup column (the paper's Table 1 compares its GPU with
+    sequential C; context only)."""
+    import torch
+    import oracle
+    from paper_1412_6862_gb300 import hd, synth
+    t_setup = time.perf_counter()
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    rows = []
+    for (M, t) in SHORT_GRID:
+        n, k, r = hd.hd_segment_params(M, t)
+        P = (SHORT_INPUT_BYTES * 8) // (t * n)
+        N = P * t
+        seed = M * 10 + t
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        data = torch.randint(-2**31, 2**31 - 1, (hd.words_for(N * k) + 4,), dtype=torch.int32, device=dev,
+                             generator=gen)
+        enc = hd.encode_short(data, n, N)
+        del data
+        host = enc.cpu().numpy().view(np.uint32).copy()
+        synth.apply_errors(host, synth.error_events(seed, n, N, p1=SHORT_P1, p2=SHORT_P2))
+        enc.copy_(torch.from_numpy(host.view(np.int32)))
+        out = torch.empty(hd.words_for(N * k) + 4, dtype=torch.int32, device=dev)
+        syn = torch.empty(N + 16, dtype=torch.int16, device=dev)
+        cnt = torch.empty(2, dtype=torch.int64, device=dev)
+        variant = hd.hd_short_autotune(n, N, 2, stream)  # at full size: larger than L2, like the run
+
+        def go():
+            rc = hd.hd_decode_short(enc.data_ptr(), N * n, n, N, out.data_ptr(), syn.data_ptr(), hd.SYN_U16,
+                                    cnt.data_ptr(), cnt.data_ptr() + 8, sh)
+            if rc != 0:
+                raise hd.HDError(rc, "hd_decode_short")
+
+        for _ in range(3):
+            go()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for _ in range(args.short_steps):
+            go()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = a.elapsed_time(b) / 1e3 / args.short_steps
+        nbytes = N * n / 8 + N * k / 8 + 2 * N
+        # oracle: 64 packets (64 t segments) on one host thread
+        Po = 64
+        o0 = time.perf_counter()
+        oracle.decode_short(host, n, Po * t, oracle.SYN_U16)
+        o_sec = time.perf_counter() - o0
+        counts = cnt.cpu().tolist()
+        rows.append({"M": M, "t": t, "n": n, "k": k, "r": r, "packets": P, "segments": N,
+                     "us_per_launch": sec * 1e6, "gbps": N * k / sec / 1e9, "packets_per_s": P / sec,
+                     "hbm_frac": nbytes / sec / 1e9 / peak, "tile_config": variant,
+                     "err_count": counts[0], "detected": counts[1],
+                     "speedup_vs_oracle_1thread": (o_sec / Po) / (sec / P)})
+        del enc, out, syn, host
+        torch.cuda.empty_cache()
+    fr = [x["hbm_frac"] for x in rows]
+    return {"workload": f"paper (M, t) grid: packets of M in {{400..2000}} bytes cut into t in {{2..6}} segments "
+                        f"(shortened Hamming codes, n = 544..8013), ~{SHORT_INPUT_BYTES >> 20} MB of segments per "
+                        f"configuration, one hd_decode_short launch each, p1={SHORT_P1}, p2={SHORT_P2} per "
+                        f"segment, u16 syndromes",
+            "hbm_frac_min": min(fr), "hbm_frac_mean": sum(fr) / len(fr), "hbm_frac_max": max(fr),
+            "grid": rows, "setup_s": time.perf_counter() - t_setup}
+
+
 def run_serving(dev, args, pool=None):
     """Open-loop Poisson arrivals of packets from the batched distribution
     (payloads pre-staged in device memory), served with continuous batching
@@ -472,6 +554,11 @@ def run_ours(args):
         res = run_serving(dev, args)
         if rank == 0:
             print(json.dumps({"serving": res}), flush=True)
+        return
+    if args.shortened_only:
+        res = run_shortened(dev, args, peaks()[0])
+        if rank == 0:
+            print(json.dumps({"shortened": res}), flush=True)
         return
 
     codes = tuple(int(c) for c in args.codes.split(","))
@@ -609,6 +696,10 @@ def run_ours(args):
     if not args.no_serve:
         serving = run_serving(dev, args, pool)
     pool = None
+    shortened = None
+    if not args.no_shortened:
+        torch.cuda.empty_cache()
+        shortened = run_shortened(dev, args, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -633,6 +724,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,
+            "shortened": shortened,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

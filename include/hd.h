@@ -145,11 +145,21 @@ hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_co
                           void *cuda_stream);
 
 /* Segments with k >= 64 are decoded by a tiled kernel compiled in several
- * configurations (warps per CTA, pipeline stages, stage bytes); these select
- * one for the current device (ordinal < 0 restores the built-in choice).  The
- * configuration never changes the result.  Host only. */
+ * configurations (warps per CTA, pipeline stages, stage bytes).  The first
+ * call for a length n on a device builds that length's output-word table
+ * (cudaMalloc plus a synchronous copy of about 2 * (k + 2200) bytes; up to 32
+ * lengths are kept per device, the least recently used one is freed after a
+ * device synchronisation), so make it before capturing a stream.
+ * hd_short_variant_select() pins one configuration for every length on the
+ * current device (ordinal < 0 removes the pin); hd_short_autotune() times
+ * every configuration on `num_codewords` all-zero segments of length n (reps
+ * launches each, 0 = 5; it allocates its own scratch buffers and synchronises
+ * `cuda_stream`) and keeps the fastest for n on the current device, returned
+ * in *chosen (-1 when n has a single kernel, k < 64).  A configuration never
+ * changes the result, only the speed. */
 hd_status hd_short_variant_count(uint32_t *count);
 hd_status hd_short_variant_select(int32_t ordinal);
+hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, void *cuda_stream, int32_t *chosen);
 
 /* ---------------------------------------------------------------------------
  * Kernel configurations and the autotuner.

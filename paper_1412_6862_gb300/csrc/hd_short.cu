@@ -568,7 +568,12 @@ constexpr int kNumShortVariants = sizeof(kShortVariants) / sizeof(kShortVariants
 constexpr uint32_t kTabSmemMax = 40u << 10;  // larger tables stay in global memory
 
 std::mutex g_short_mu;
-int g_short_choice[64] = {};  // selected variant per device (index + 1; 0 = default)
+int g_short_choice[64] = {};  // variant pinned for every length on a device (index + 1; 0 = none)
+struct TunedEntry {
+    uint32_t n = 0;
+    int v = -1;
+};
+TunedEntry g_short_tuned[64][64];  // per device: the autotuner's choice per length
 
 struct OccEntry {
     int v = -1, tsm = 0;
@@ -605,13 +610,36 @@ int short_blocks_per_sm(int v, int tsm, uint32_t smem)
     return bps;
 }
 
-int current_short_variant()
+// The configuration for length n: a pinned one, else the autotuner's, else the built-in default.
+int current_short_variant(uint32_t n)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
     std::lock_guard<std::mutex> lk(g_short_mu);
-    return g_short_choice[dev] > 0 ? g_short_choice[dev] - 1 : 0;
+    if (g_short_choice[dev] > 0) return g_short_choice[dev] - 1;
+    for (const TunedEntry &e : g_short_tuned[dev])
+        if (e.n == n && e.v >= 0) return e.v;
+    return 0;
+}
+
+void remember_short_variant(uint32_t n, int v)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    TunedEntry *slot = nullptr;
+    for (TunedEntry &e : g_short_tuned[dev]) {
+        if (e.n == n) {
+            slot = &e;
+            break;
+        }
+        if (!slot && e.v < 0) slot = &e;
+    }
+    if (!slot) slot = &g_short_tuned[dev][n % 64];  // table full: overwrite one entry
+    slot->n = n;
+    slot->v = v;
 }
 
 // Team size of the syndrome pass: a team of T lanes reads a codeword's Y
@@ -829,7 +857,7 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
     const uint32_t r = short_r(n), k = n - r;
     const int syn = syndromes ? (int)syn_type : 0;
     if (k >= kLongMinK) {
-        int vi = current_short_variant();
+        int vi = current_short_variant(n);
         if (kShortVariants[vi].SB * 8u < n + 256u) vi = 1;  // stage too small for one codeword: largest stage
         if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
                                st) != cudaSuccess)
@@ -861,6 +889,65 @@ hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_co
                                                              num_codewords, stream);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, void *cuda_stream, int32_t *chosen)
+{
+    if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
+    const uint32_t r = short_r(n), k = n - r;
+    if (num_codewords == 0 || num_codewords > (1ull << 32)) return HD_ERR_SIZE;
+    if (reps == 0) reps = 5;
+    if (k < kLongMinK) {  // one kernel only
+        if (chosen) *chosen = -1;
+        return HD_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t in_b = words_for_bits(num_codewords * n) * 4 + 16, out_b = words_for_bits(num_codewords * k) * 4 + 16;
+    void *din = nullptr, *dout = nullptr, *dsyn = nullptr, *dcnt = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hd_status rc = HD_OK;
+    int best = -1;
+    float best_ms = 0.f;
+    if (cudaMalloc(&din, in_b) != cudaSuccess || cudaMalloc(&dout, out_b) != cudaSuccess ||
+        cudaMalloc(&dsyn, num_codewords * 2 + 16) != cudaSuccess || cudaMalloc(&dcnt, 16) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = HD_ERR_CUDA;
+    // all-zero segments are codewords: the timing sees the common no-error path
+    if (rc == HD_OK && cudaMemsetAsync(din, 0, in_b, st) != cudaSuccess) rc = HD_ERR_CUDA;
+    auto *cnt = static_cast<unsigned long long *>(dcnt);
+    for (int v = 0; rc == HD_OK && v < kNumShortVariants; ++v) {
+        if (kShortVariants[v].SB * 8u < n + 256u) continue;
+        auto go = [&]() {
+            return launch_short_tiles(v, static_cast<const uint32_t *>(din), n, num_codewords,
+                                      static_cast<uint32_t *>(dout), dsyn, HD_SYN_U16, cnt, cnt + 1, st);
+        };
+        if (go() != cudaSuccess) {  // warm-up (also configures the kernel)
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        cudaEventRecord(e0, st);
+        for (uint32_t i = 0; i < reps; ++i) go();
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = HD_ERR_CUDA;
+            break;
+        }
+        if (best < 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    if (dsyn) cudaFree(dsyn);
+    if (dcnt) cudaFree(dcnt);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != HD_OK) return rc;
+    if (best >= 0) remember_short_variant(n, best);
+    if (chosen) *chosen = best;
+    return HD_OK;
 }
 
 hd_status hd_short_variant_count(uint32_t *count)

@@ -122,6 +122,7 @@ SIGNATURES = {
     "hd_encode_short": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_short_variant_count": (_i32, [_c.POINTER(_u32)]),
     "hd_short_variant_select": (_i32, [_c.c_int32]),
+    "hd_short_autotune": (_i32, [_u32, _u64, _u32, _vp, _c.POINTER(_c.c_int32)]),
     "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -475,6 +476,14 @@ def hd_short_variant_count() -> int:
 
 def hd_short_variant_select(ordinal: int) -> None:
     check(lib().hd_short_variant_select(ordinal), "hd_short_variant_select")
+
+
+def hd_short_autotune(n: int, num_codewords: int, reps: int = 5, cuda_stream=None) -> int:
+    """Time every tile configuration for length n; returns the chosen ordinal (-1: single kernel)."""
+    chosen = _c.c_int32(-2)
+    check(lib().hd_short_autotune(n, num_codewords, reps, _stream_handle(cuda_stream), ctypes.byref(chosen)),
+          "hd_short_autotune")
+    return int(chosen.value)
 
 
 def decode_short(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U16, out=None, syndromes=None,

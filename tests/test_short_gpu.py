@@ -209,3 +209,14 @@ def test_alternating_lengths():
     # shorter one must still launch (and give the same bits)
     for n in (8013, 300, 4096, 8013, 71, 32767, 545):
         _check(n, 97 if n < 10000 else 9, hd.SYN_U16, seed=n + 31)
+
+
+def test_autotune_keeps_parity():
+    try:
+        for n in (2679, 544, 8013):
+            v = hd.hd_short_autotune(n, 20000, 2)
+            assert 0 <= v < hd.hd_short_variant_count()
+            _check(n, 777 if n < 5000 else 200, hd.SYN_U16, seed=n + 5)
+        assert hd.hd_short_autotune(33, 1000, 1) == -1  # k < 64: a single kernel
+    finally:
+        hd.hd_short_variant_select(-1)
