@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-shortened", action="store_true", help="skip the shortened-code (M, t) grid section")
     ap.add_argument("--shortened-only", action="store_true", help="run only the shortened-code section")
     ap.add_argument("--short-steps", type=int, default=10, help="timed launches per (M, t) configuration")
+    ap.add_argument("--short-grid", type=str, default="", help="subset of the (M, t) grid, e.g. 2000:2,400:6")
+    ap.add_argument("--short-no-autotune", action="store_true", help="keep the built-in tile configuration")
     return ap.parse_args()
 
 
@@ -437,7 +439,10 @@ def run_shortened(dev, args, peak):
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     rows = []
-    for (M, t) in SHORT_GRID:
+    grid = SHORT_GRID
+    if args.short_grid:
+        grid = [tuple(int(v) for v in item.split(":")) for item in args.short_grid.split(",")]
+    for (M, t) in grid:
         n, k, r = hd.hd_segment_params(M, t)
         P = (SHORT_INPUT_BYTES * 8) // (t * n)
         N = P * t
@@ -454,7 +459,7 @@ def run_shortened(dev, args, peak):
         out = torch.empty(hd.words_for(N * k) + 4, dtype=torch.int32, device=dev)
         syn = torch.empty(N + 16, dtype=torch.int16, device=dev)
         cnt = torch.empty(2, dtype=torch.int64, device=dev)
-        variant = hd.hd_short_autotune(n, N, 2, stream)  # at full size: larger than L2, like the run
+        variant = -1 if args.short_no_autotune else hd.hd_short_autotune(n, N, 2, stream)  # at full size, > L2
 
         def go():
             rc = hd.hd_decode_short(enc.data_ptr(), N * n, n, N, out.data_ptr(), syn.data_ptr(), hd.SYN_U16,
