@@ -75,6 +75,14 @@ class Oracle:
         L.hd_ref_decode_short_range.restype = ctypes.c_int
         L.hd_ref_encode_short.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
         L.hd_ref_encode_short.restype = ctypes.c_int
+        L.hd_ref_decode_secded.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, u32p,
+                                           ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.hd_ref_decode_secded.restype = ctypes.c_int
+        L.hd_ref_decode_secded_range.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, u32p,
+                                                 ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.hd_ref_decode_secded_range.restype = ctypes.c_int
+        L.hd_ref_encode_secded.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
+        L.hd_ref_encode_secded.restype = ctypes.c_int
         self.lib = L
         self.path = path
 
@@ -191,6 +199,64 @@ class Oracle:
             syn = syn[:num_codewords]
         return out, syn, c, d
 
+    # -- SECDED: full-length code plus an overall parity bit at position 0 ---
+    def encode_secded(self, data_words: np.ndarray, n: int, num_codewords: int) -> np.ndarray:
+        m = self.lib.hd_ref_num_checksum_bits(n)
+        if m == 0:
+            raise ValueError(f"unsupported n={n}")
+        k = n - m
+        data = np.ascontiguousarray(data_words, dtype=np.uint32)
+        if data.size < words_for(num_codewords * k):
+            raise ValueError("data buffer too small")
+        out = np.zeros(max(1, words_for(num_codewords * (n + 1))), dtype=np.uint32)
+        rc = self.lib.hd_ref_encode_secded(_u32p(data), n, num_codewords, _u32p(out))
+        if rc != 0:
+            raise RuntimeError(f"hd_ref_encode_secded failed: {rc}")
+        return out[:words_for(num_codewords * (n + 1))]
+
+    def decode_secded(self, stream: np.ndarray, n: int, num_codewords: int, syn_type: int = SYN_U16,
+                      threads: int = 1):
+        """Decode an extended-Hamming stream: (data words, syndromes, err_count, detected).
+        Syndrome values are s | P << m."""
+        m = self.lib.hd_ref_num_checksum_bits(n)
+        if m == 0:
+            raise ValueError(f"unsupported n={n}")
+        k = n - m
+        s = np.ascontiguousarray(stream, dtype=np.uint32)
+        out = np.zeros(max(1, words_for(num_codewords * k)), dtype=np.uint32)
+        syn = None
+        if syn_type == SYN_U8:
+            syn = np.zeros(max(1, num_codewords), dtype=np.uint8)
+        elif syn_type == SYN_U16:
+            syn = np.zeros(max(1, num_codewords), dtype=np.uint16)
+        synp = None if syn is None else syn.ctypes.data_as(ctypes.c_void_p)
+        if threads <= 1 or num_codewords < 64:
+            ce, de = ctypes.c_uint64(0), ctypes.c_uint64(0)
+            rc = self.lib.hd_ref_decode_secded(_u32p(s), (n + 1) * num_codewords, n, num_codewords, _u32p(out),
+                                               synp, syn_type, ctypes.byref(ce), ctypes.byref(de))
+            if rc != 0:
+                raise RuntimeError(f"hd_ref_decode_secded failed: {rc}")
+            c, d = int(ce.value), int(de.value)
+        else:
+            per = max(32, ((num_codewords + threads - 1) // threads + 31) // 32 * 32)
+            ranges = [(a, min(per, num_codewords - a)) for a in range(0, num_codewords, per)]
+
+            def run(rg):
+                ce, de = ctypes.c_uint64(0), ctypes.c_uint64(0)
+                rc = self.lib.hd_ref_decode_secded_range(_u32p(s), n, rg[0], rg[1], _u32p(out), synp, syn_type,
+                                                         ctypes.byref(ce), ctypes.byref(de))
+                if rc != 0:
+                    raise RuntimeError(f"hd_ref_decode_secded_range failed: {rc}")
+                return int(ce.value), int(de.value)
+
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                res = list(ex.map(run, ranges))
+            c, d = sum(x[0] for x in res), sum(x[1] for x in res)
+        out = out[:words_for(num_codewords * k)]
+        if syn is not None:
+            syn = syn[:num_codewords]
+        return out, syn, c, d
+
     def decode_threaded(self, stream: np.ndarray, n: int, num_codewords: int, syn_type: int,
                         threads: int, out: np.ndarray, syn: np.ndarray | None) -> int:
         """Decode with ``threads`` host threads over 32-codeword-aligned ranges.
@@ -263,3 +329,11 @@ def encode_short(data_words, n, num_codewords):
 
 def decode_short(stream, n, num_codewords, syn_type=SYN_U16, threads=1):
     return default().decode_short(stream, n, num_codewords, syn_type, threads)
+
+
+def encode_secded(data_words, n, num_codewords):
+    return default().encode_secded(data_words, n, num_codewords)
+
+
+def decode_secded(stream, n, num_codewords, syn_type=SYN_U16, threads=1):
+    return default().decode_secded(stream, n, num_codewords, syn_type, threads)

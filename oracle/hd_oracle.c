@@ -259,6 +259,111 @@ int hd_ref_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_code
     return REF_OK;
 }
 
+/* ---------------------------------------------------------------------------
+ * SECDED (extended Hamming): not in the paper.  A full-length code n = 2^m - 1
+ * plus an overall parity bit at position 0, so a codeword has n + 1 = 2^m
+ * bits: codeword i occupies stream bits [i*(n+1), (i+1)*(n+1)) with position p
+ * (0..n) at bit i*(n+1) + p.  Even parity over all n + 1 bits.
+ *   s = XOR of the positions 1..n of the set bits, P = parity of all n + 1 bits.
+ *   P = 1: one error; flip position s (s = 0: the overall parity bit itself).
+ *   P = 0, s != 0: two errors, detected; the codeword is left as received.
+ * The syndrome value is s | P << m; err_count counts nonzero values, detected
+ * counts P = 0 with s != 0.
+ * ------------------------------------------------------------------------- */
+int hd_ref_decode_secded_range(const uint32_t *stream, uint32_t n, uint64_t first, uint64_t count, uint32_t *out_bits,
+                               void *syndromes, int syn_type, uint64_t *errs, uint64_t *detected)
+{
+    int m = hd_ref_num_checksum_bits(n);
+    if (m == 0) return REF_ERR_INVALID_N;
+    if (count == 0) return REF_OK;
+    if (!stream || !out_bits || !errs || !detected) return REF_ERR_NULL;
+    uint32_t k = n - (uint32_t)m, len = n + 1u;
+    unsigned char bit[256];
+    uint64_t ce = 0, de = 0;
+    for (uint64_t i = first; i < first + count; ++i) {
+        for (uint32_t p = 0; p <= n; ++p)
+            bit[p] = (unsigned char)get_bit(stream, i * len + p);
+        uint32_t s = 0, par = 0;
+        for (uint32_t p = 0; p <= n; ++p) {
+            if (bit[p]) {
+                s ^= p;
+                par ^= 1u;
+            }
+        }
+        uint32_t v = s | (par << m);
+        if (v != 0) ++ce;
+        if (par)
+            bit[s] ^= 1u; /* one error: position s (0 is the overall parity bit) */
+        else if (s != 0)
+            ++de; /* two errors: detected, not corrected */
+        uint32_t d = 0;
+        for (uint32_t p = 1; p <= n; ++p) {
+            if (is_checksum_position(p)) continue;
+            put_bit(out_bits, i * k + d, bit[p]);
+            ++d;
+        }
+        if (syn_type == REF_SYN_U8 && syndromes)
+            ((uint8_t *)syndromes)[i] = (uint8_t)v;
+        else if (syn_type == REF_SYN_U16 && syndromes)
+            ((uint16_t *)syndromes)[i] = (uint16_t)v;
+    }
+    *errs += ce;
+    *detected += de;
+    return REF_OK;
+}
+
+int hd_ref_decode_secded(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                         uint32_t *out_bits, void *syndromes, int syn_type, uint64_t *err_count, uint64_t *detected)
+{
+    int m = hd_ref_num_checksum_bits(n);
+    if (m == 0) return REF_ERR_INVALID_N;
+    if (in_bits != (uint64_t)(n + 1u) * num_codewords) return REF_ERR_SIZE;
+    uint64_t ce = 0, de = 0;
+    if (num_codewords > 0) {
+        int rc = hd_ref_decode_secded_range(stream, n, 0, num_codewords, out_bits, syndromes, syn_type, &ce, &de);
+        if (rc != REF_OK) return rc;
+        zero_pad(out_bits, num_codewords * (uint64_t)(n - (uint32_t)m));
+    }
+    if (err_count) *err_count = ce;
+    if (detected) *detected = de;
+    return REF_OK;
+}
+
+/* SECDED encoder (test inputs only): the Hamming checksum bits, then the
+ * overall parity bit at position 0 makes the parity of all n + 1 bits even. */
+int hd_ref_encode_secded(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream)
+{
+    int m = hd_ref_num_checksum_bits(n);
+    if (m == 0) return REF_ERR_INVALID_N;
+    if (num_codewords == 0) return REF_OK;
+    if (!data_bits || !stream) return REF_ERR_NULL;
+    uint32_t k = n - (uint32_t)m, len = n + 1u;
+    unsigned char bit[256];
+    for (uint64_t i = 0; i < num_codewords; ++i) {
+        uint32_t d = 0;
+        for (uint32_t p = 1; p <= n; ++p) {
+            if (is_checksum_position(p)) {
+                bit[p] = 0;
+            } else {
+                bit[p] = (unsigned char)get_bit(data_bits, i * k + d);
+                ++d;
+            }
+        }
+        uint32_t s = 0;
+        for (uint32_t p = 1; p <= n; ++p)
+            if (bit[p]) s ^= p;
+        for (int j = 0; j < m; ++j)
+            bit[1u << j] = (unsigned char)(1u & (s >> j) & 1u);
+        uint32_t par = 0;
+        for (uint32_t p = 1; p <= n; ++p) par ^= bit[p];
+        bit[0] = (unsigned char)par;
+        for (uint32_t p = 0; p <= n; ++p)
+            put_bit(stream, i * len + p, bit[p]);
+    }
+    zero_pad(stream, num_codewords * (uint64_t)len);
+    return REF_OK;
+}
+
 /* Encoder, used only to build test inputs (Sec. II: the transmitter adds the
  * checksum bits to the message).  Per codeword: the k data bits go to the
  * non-power-of-two positions in increasing order, the checksum positions start

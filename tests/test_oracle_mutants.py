@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as pins
+from tests import test_oracle_secded as secded_pins
 from tests import test_oracle_short as short_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hd_oracle.c")
@@ -66,6 +67,47 @@ def _pin_suite(o):
     return failed
 
 
+# Mistakes in the SECDED functions, caught by the pins of ``test_oracle_secded.py``.
+SECDED_MUTANTS = {
+    "secded_parity_skips_position_0": ("        for (uint32_t p = 0; p <= n; ++p) {\n            if (bit[p]) {\n                s ^= p;\n                par ^= 1u;",
+                                       "        for (uint32_t p = 1; p <= n; ++p) {\n            if (bit[p]) {\n                s ^= p;\n                par ^= 1u;"),
+    "secded_corrects_double_errors": ("        if (par)\n            bit[s] ^= 1u; /* one error",
+                                      "        if (par || s)\n            bit[s] ^= 1u; /* one error"),
+    "secded_detects_on_odd_parity": ("        else if (s != 0)\n            ++de; /* two errors",
+                                     "        if (s != 0)\n            ++de; /* two errors"),
+    "secded_encoder_parity_of_data_only": ("        for (uint32_t p = 1; p <= n; ++p) par ^= bit[p];",
+                                           "        for (uint32_t p = 3; p <= n; ++p) par ^= (p & (p - 1u)) ? bit[p] : 0u;"),
+    "secded_syndrome_without_parity_bit": ("        uint32_t v = s | (par << m);", "        uint32_t v = s;"),
+}
+
+
+def _secded_pin_suite(o):
+    checks = [
+        ("brute_7", lambda: secded_pins.test_secded_bruteforce(o, 7)),
+        ("relation_31", lambda: secded_pins.test_secded_relation_to_single_error_decoder(o, 31)),
+        ("matrix_63", lambda: secded_pins.test_secded_matrix_form(o, 63)),
+        ("events", lambda: secded_pins.test_secded_injected_events(o)),
+    ]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:
+            failed.append(name)
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(SECDED_MUTANTS))
+def test_secded_mutant_is_caught(tmp_path, name):
+    old, new = SECDED_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation anchor not unique: {old}"
+    src = tmp_path / "hd_oracle.c"
+    src.write_text(text.replace(old, new, 1))
+    lib = oracle.build(force=True, src=str(src), out=str(tmp_path / "lib.so"))
+    assert _secded_pin_suite(oracle.Oracle(lib)), f"mutant {name} passed every pin"
+
+
 def _short_pin_suite(o):
     checks = [
         ("params", lambda: short_pins.test_short_params_are_minimal(o)),
@@ -89,6 +131,7 @@ def test_unmutated_copy_passes(tmp_path):
     lib = oracle.build(force=True, src=str(src), out=str(tmp_path / "lib.so"))
     assert _pin_suite(oracle.Oracle(lib)) == []
     assert _short_pin_suite(oracle.Oracle(lib)) == []
+    assert _secded_pin_suite(oracle.Oracle(lib)) == []
 
 
 @pytest.mark.parametrize("name", sorted(SHORT_MUTANTS))
