@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--short-steps", type=int, default=10, help="timed launches per (M, t) configuration")
     ap.add_argument("--short-grid", type=str, default="", help="subset of the (M, t) grid, e.g. 2000:2,400:6")
     ap.add_argument("--short-no-autotune", action="store_true", help="keep the built-in tile configuration")
+    ap.add_argument("--no-secded", action="store_true", help="skip the SECDED section")
+    ap.add_argument("--secded-only", action="store_true", help="run only the SECDED section")
+    ap.add_argument("--secded-codes", type=str, default="15,31,63,127,255")
     return ap.parse_args()
 
 
@@ -500,6 +503,72 @@ def run_shortened(dev, args, peak):
             "grid": rows, "setup_s": time.perf_counter() - t_setup}
 
 
+SECDED_P1, SECDED_P2 = 0.05, 0.005
+
+
+def run_secded(dev, args, peak):
+    """SECDED (extended Hamming, not in the paper) against the plain decoder on
+    the same code lengths: 2^24 codewords (n <= 63) or 2^22 (n >= 127), GPU
+    encoder, p1/p2 channel errors over the n + 1 bits, u16 syndromes, 10 timed
+    launches of each.  Algorithmic bytes per codeword: (n+1)/8 + k/8 + 2."""
+    import torch
+    from paper_1412_6862_gb300 import hd, synth
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    res = {}
+    for n in (int(c) for c in args.secded_codes.split(",")):
+        m, k = hd.code_params(n)
+        N = (1 << 24) if n <= 63 else (1 << 22)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1000 + n)
+        data = torch.randint(-2**31, 2**31 - 1, (hd.words_for(N * k) + 4,), dtype=torch.int32, device=dev,
+                             generator=gen)
+        enc = hd.encode_secded(data, n, N)
+        host = enc.cpu().numpy().view(np.uint32).copy()
+        synth.apply_errors(host, synth.error_events(1000 + n, n + 1, N, p1=SECDED_P1, p2=SECDED_P2))
+        enc.copy_(torch.from_numpy(host.view(np.int32)))
+        plain = hd.encode(data, n, N)
+        out = torch.empty(hd.words_for(N * k) + 4, dtype=torch.int32, device=dev)
+        syn = torch.empty(N + 16, dtype=torch.int16, device=dev)
+        cnt = torch.empty(2, dtype=torch.int64, device=dev)
+        del data, host
+
+        def go_x():
+            hd.check(hd.hd_decode_secded(enc.data_ptr(), N * (n + 1), n, N, out.data_ptr(), syn.data_ptr(),
+                                         hd.SYN_U16, cnt.data_ptr(), cnt.data_ptr() + 8, sh), "hd_decode_secded")
+
+        def go_p():
+            hd.check(hd.hd_decode(plain.data_ptr(), N * n, n, N, out.data_ptr(), syn.data_ptr(), hd.SYN_U16,
+                                  cnt.data_ptr(), sh), "hd_decode")
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            for _ in range(10):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            return a.elapsed_time(b) / 1e3 / 10
+
+        tx = timed(go_x)
+        counts = cnt.cpu().tolist()
+        tp = timed(go_p)
+        bx = N * (n + 1) / 8 + N * k / 8 + 2 * N
+        bp = N * n / 8 + N * k / 8 + 2 * N
+        res[str(n)] = {"codewords": N, "secded_us": tx * 1e6, "secded_gbps": N * k / tx / 1e9,
+                       "secded_hbm_frac": bx / tx / 1e9 / peak, "plain_us": tp * 1e6,
+                       "plain_gbps": N * k / tp / 1e9, "plain_hbm_frac": bp / tp / 1e9 / peak,
+                       "err_count": counts[0], "detected": counts[1]}
+        del enc, plain, out, syn
+        torch.cuda.empty_cache()
+    return {"workload": f"SECDED (extended Hamming, overall parity at position 0) vs plain Hamming, 2^24 "
+                        f"codewords (n <= 63) or 2^22 (n >= 127), p1={SECDED_P1}, p2={SECDED_P2} per codeword, "
+                        f"u16 syndromes; one hd_decode_secded / hd_decode launch each", "codes": res}
+
+
 def run_serving(dev, args, pool=None):
     """Open-loop Poisson arrivals of packets from the batched distribution
     (payloads pre-staged in device memory), served with continuous batching
@@ -559,6 +628,11 @@ def run_ours(args):
         res = run_serving(dev, args)
         if rank == 0:
             print(json.dumps({"serving": res}), flush=True)
+        return
+    if args.secded_only:
+        res = run_secded(dev, args, peaks()[0])
+        if rank == 0:
+            print(json.dumps({"secded": res}), flush=True)
         return
     if args.shortened_only:
         res = run_shortened(dev, args, peaks()[0])
@@ -705,6 +779,10 @@ def run_ours(args):
     if not args.no_shortened:
         torch.cuda.empty_cache()
         shortened = run_shortened(dev, args, peak)
+    secded = None
+    if not args.no_secded:
+        torch.cuda.empty_cache()
+        secded = run_secded(dev, args, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -730,6 +808,7 @@ def run_ours(args):
             "batched": batched,
             "serving": serving,
             "shortened": shortened,
+            "secded": secded,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

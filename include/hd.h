@@ -162,6 +162,32 @@ hd_status hd_short_variant_select(int32_t ordinal);
 hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, void *cuda_stream, int32_t *chosen);
 
 /* ---------------------------------------------------------------------------
+ * SECDED (extended Hamming codes).  Not in the paper: an extension of its
+ * single-error decoder that detects double errors instead of miscorrecting
+ * them.  A full-length code n = 2^m - 1 (n = 7..255) plus an overall parity
+ * bit at position 0: codeword i occupies stream bits [i*(n+1), (i+1)*(n+1))
+ * with position p (0..n) at bit i*(n+1) + p; even parity over all n + 1 bits;
+ * the n - m data bits are the non-power-of-two positions as in hd_decode().
+ * ------------------------------------------------------------------------- */
+
+/* Decode `num_codewords` SECDED codewords.  in_bits must equal
+ * (n + 1) * num_codewords.  With s the checksum vector of positions 1..n and
+ * P the parity of all n + 1 bits: P = 1 flips position s (s = 0: the parity
+ * bit itself, the data are intact); P = 0 with s != 0 is a detected double
+ * error, left as received and counted in *detected_count.  Syndrome element i
+ * is s | P << m (HD_SYN_U8 only for n <= 127); *err_count counts nonzero
+ * elements.  Other arguments, layout, counters and errors as hd_decode(). */
+hd_status hd_decode_secded(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                           uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                           unsigned long long *err_count, unsigned long long *detected_count, void *cuda_stream);
+
+/* Encode `num_codewords` messages of n - m bits into SECDED codewords (as
+ * hd_encode(), with the overall parity bit at position 0; stream pad bits are
+ * written as 0). */
+hd_status hd_encode_secded(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
+                           void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel configurations and the autotuner.
  *
  * Long streams are decoded by a streaming kernel compiled in several

@@ -75,11 +75,11 @@ template <int N_, int SYN>
 __device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sbuf, int lane, uint32_t chunks)
 {
     using Q = ChunkGeom<N_, SYN, batch_G(N_)>;
-    uint32_t e = 0;
+    uint32_t e = 0, unused = 0;
     for (uint32_t c = 0; c < chunks; ++c)
         e += decode_warp_chunk<N_, SYN, batch_G(N_)>(stage + c * Q::in_words,
                                                       const_cast<uint32_t *>(stage) + c * Q::out_words,
-                                                      sbuf + c * Q::syn_bytes, lane);
+                                                      sbuf + c * Q::syn_bytes, lane, unused);
     return e;
 }
 

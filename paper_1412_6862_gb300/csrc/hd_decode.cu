@@ -16,6 +16,7 @@ namespace hd {
 void register_stream_a(std::vector<StreamVariant> &v);
 void register_stream_b(std::vector<StreamVariant> &v);
 void register_stream_c(std::vector<StreamVariant> &v);
+void register_stream_secded(std::vector<StreamVariant> &v);
 
 namespace {
 
@@ -30,6 +31,16 @@ const std::vector<StreamVariant> &variants()
         register_stream_a(a);
         register_stream_b(a);
         register_stream_c(a);
+        return a;
+    }();
+    return v;
+}
+
+const std::vector<StreamVariant> &secded_variants()
+{
+    static const std::vector<StreamVariant> v = [] {
+        std::vector<StreamVariant> a;
+        register_stream_secded(a);
         return a;
     }();
     return v;
@@ -140,7 +151,26 @@ cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, 
     uint32_t *status = status_ptr();
     if (status == nullptr) return cudaErrorInvalidSymbol;
     *covered = nchunks * v.chunk_cw;
-    return v.launch(v, in, nchunks, out, syn, err, status, st);
+    return v.launch(v, in, nchunks, out, syn, err, status, st, nullptr);
+}
+
+// SECDED: the streaming kernel with codewords of n + 1 bits, compiled in the
+// built-in configuration of n for each syndrome type.
+cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
+                                      int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
+                                      uint64_t *covered)
+{
+    *covered = 0;
+    const StreamVariant *v = nullptr;
+    for (const StreamVariant &x : secded_variants())
+        if (x.n == n && x.syn == syn_type) v = &x;
+    if (v == nullptr) return cudaSuccess;
+    const uint64_t nchunks = num_cw / v->chunk_cw;
+    if (nchunks == 0) return cudaSuccess;
+    uint32_t *status = status_ptr();
+    if (status == nullptr) return cudaErrorInvalidSymbol;
+    *covered = nchunks * v->chunk_cw;
+    return v->launch(*v, in, nchunks, out, syn, err, status, st, det);
 }
 
 // ---------------------------------------------------------------------------
@@ -274,13 +304,14 @@ hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, 
         void *sy = syn_type == HD_SYN_NONE ? nullptr : dsyn;
         auto *er = static_cast<unsigned long long *>(derr);
         if (v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status,
-                     st) != cudaSuccess) {
+                     st, nullptr) != cudaSuccess) {
             rc = HD_ERR_CUDA;
             break;
         }
         cudaEventRecord(e0, st);
         for (uint32_t r = 0; r < reps; ++r)
-            v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status, st);
+            v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status, st,
+                     nullptr);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = HD_ERR_CUDA;

@@ -41,6 +41,12 @@ cudaError_t launch_encode_generic(const uint32_t *data, uint64_t data_words, uin
 cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
                                int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered);
 
+// The SECDED streaming decoder (codewords of n + 1 bits): whole chunks, as
+// launch_decode_fast; `det` (or nullptr) receives the detected double errors.
+cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
+                                      int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
+                                      uint64_t *covered);
+
 // Device address of the status word that kernels latch HD_ERR_TIMEOUT into
 // (per device; nullptr on failure), and its host-side read-and-clear.
 uint32_t *status_ptr();

@@ -192,14 +192,16 @@ void scheduler(hd_server *s)
                 s->stats.max_resident_bytes = std::max(s->stats.max_resident_bytes, s->resident);
                 s->stats.waves += 1;
                 s->wave_packets_sum += w.reqs.size();
+                // busy before the lock is released: hd_server_drain() must never see these
+                // requests neither pending nor in a busy wave
+                w.busy = true;
+                s->busy_waves.fetch_add(1);
             }
             w.t_admit = now_ns();
             if (!launch_wave(s, w)) {
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->error = HD_ERR_CUDA;
             }
-            w.busy = true;
-            s->busy_waves.fetch_add(1);
             progress = true;
         }
         if (progress) continue;

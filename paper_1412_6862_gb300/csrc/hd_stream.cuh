@@ -35,23 +35,35 @@ struct StreamVariant {
     uint32_t smem;
     uint64_t chunk_cw;  // codewords per warp iteration (32*G)
     cudaError_t (*launch)(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out, void *syn,
-                          unsigned long long *err, uint32_t *status, cudaStream_t st);
+                          unsigned long long *err, uint32_t *status, cudaStream_t st, unsigned long long *det);
     const void *kernel;
+    int xh = 0;  // SECDED: codewords of n + 1 bits with the overall parity bit at position 0
 };
 
-// Geometry of one warp chunk of code n: 32*G codewords, G tiles of 32.
-template <int N_, int SYN, int G>
+// Geometry of one warp chunk of code n: 32*G codewords, G tiles of 32.  XH:
+// SECDED codewords of L = n + 1 bits (32 of them fill L words).
+template <int N_, int SYN, int G, bool XH = false>
 struct ChunkGeom {
     using C = Code<N_>;
-    static constexpr int H = 32 / G;                      // threads per 32-codeword tile
-    static constexpr int TEAMS = G;                       // tiles per warp chunk
-    static constexpr int SB = SYN == 2 ? 2 : 1;           // syndrome bytes (packing width)
-    static constexpr bool WIDE = (SB == 1 && C::m == 8);  // u8 lanes may use bit 7
-    static constexpr int GK = G * C::k;                   // output bits per thread
+    static constexpr int L = N_ + (XH ? 1 : 0);                       // input bits per codeword
+    static constexpr int H = 32 / G;                                  // threads per 32-codeword tile
+    static constexpr int TEAMS = G;                                   // tiles per warp chunk
+    static constexpr int SB = SYN == 2 ? 2 : 1;                       // syndrome bytes (packing width)
+    static constexpr bool WIDE = (SB == 1 && C::m + (XH ? 1 : 0) == 8);  // u8 lanes may use bit 7
+    static constexpr int GK = G * C::k;                               // output bits per thread
     static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
-    static constexpr int R = (G * N_ + 31) / 32;          // input words per thread after re-alignment
-    static constexpr uint32_t in_words = TEAMS * N_;
+    static constexpr int R = (G * L + 31) / 32;                       // input words per thread after re-alignment
+    static constexpr uint32_t in_words = TEAMS * L;
     static constexpr uint32_t in_bytes = in_words * 4;
+    // PADDED (SECDED with n >= 127): each thread's part (R words, whole codewords) has its own
+    // stage slot of R + 4 words, loaded by its own bulk copy, so that 128-bit reads of the 32
+    // parts fall on distinct banks (a part stride that is a multiple of 32 words would put every
+    // lane on the same bank).  For shorter SECDED codewords one bulk copy per chunk measured
+    // faster on GB300 despite the conflicts.
+    static constexpr bool PADDED = XH && N_ >= 127;
+    static constexpr uint32_t part_words = R + 4;
+    static constexpr uint32_t stage_payload = PADDED ? 32 * part_words * 4 : in_bytes;
+    static_assert(!PADDED || (R % 4 == 0 && 32 * R == (int)in_words), "padded parts are whole 16-byte groups");
     static constexpr uint32_t out_words = TEAMS * C::k;
     static constexpr uint32_t out_bytes = out_words * 4;
     static constexpr uint32_t syn_bytes = SYN ? 32 * G * SB : 0;
@@ -67,18 +79,29 @@ struct ChunkGeom {
 // equal `stage`: every lane copies its part to registers and the warp
 // synchronises before the first write) and its syndromes at `sbase`.  Returns
 // this lane's count of nonzero syndromes.
-template <int N_, int SYN, int G>
-__device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uint32_t *obase, uint8_t *sbase, int lane)
+template <int N_, int SYN, int G, bool XH = false>
+__device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uint32_t *obase, uint8_t *sbase, int lane,
+                                                      uint32_t &det)
 {
-    using Q = ChunkGeom<N_, SYN, G>;
+    using Q = ChunkGeom<N_, SYN, G, XH>;
     constexpr int H = Q::H;
     const int team = lane / H, h = lane % H;
-    const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * N_);
-    const uint32_t in_w = team * N_ + (in_bit >> 5), in_sh = in_bit & 31u;
+    const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * Q::L);
+    const uint32_t in_w = team * Q::L + (in_bit >> 5), in_sh = in_bit & 31u;
     const uint32_t out_bit = (uint32_t)h * (uint32_t)Q::GK;
     const uint32_t out_w = team * Code<N_>::k + (out_bit >> 5), out_sh = out_bit & 31u;
     uint32_t r[Q::R];
-    if constexpr (H == 1) {
+    if constexpr (Q::PADDED) {
+        const uint4 *part = reinterpret_cast<const uint4 *>(stage + lane * Q::part_words);
+#pragma unroll
+        for (int t = 0; t < Q::R / 4; ++t) {
+            const uint4 v = part[t];
+            r[4 * t] = v.x;
+            r[4 * t + 1] = v.y;
+            r[4 * t + 2] = v.z;
+            r[4 * t + 3] = v.w;
+        }
+    } else if constexpr (H == 1) {
 #pragma unroll
         for (int w = 0; w < Q::R; ++w) r[w] = stage[in_w + w];
     } else {
@@ -93,7 +116,7 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
     __syncwarp();  // the whole chunk is in registers
     OutPacker<Q::GK, Q::ALIGNED, Q::V> op(obase + out_w, out_sh);
     SynPacker<Q::SB, SYN != 0, G, Q::WIDE> sp(sbase + (uint32_t)lane * G * Q::SB);
-    decode_part<N_, G, Q::R>(r, op, sp);
+    decode_part<N_, G, Q::R, XH>(r, op, sp, det);
     return sp.nonzero();
 }
 
@@ -101,11 +124,11 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
 // mbarrier each, (unless INPLACE) two output staging buffers, and two syndrome
 // buffers.  Lane 0 issues the warp's bulk loads and stores; warps never wait
 // for one another, so one warp's memory wait overlaps the others' arithmetic.
-template <int N_, int SYN, int T, int S, int G, int INPLACE>
-struct StreamCfg : ChunkGeom<N_, SYN, G> {
-    using Q = ChunkGeom<N_, SYN, G>;
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
+struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
+    using Q = ChunkGeom<N_, SYN, G, XH>;
     static constexpr int WARPS = T / 32;
-    static constexpr uint32_t stage_bytes = Q::in_bytes + 16;  // one spare 16-byte group for the funnel read
+    static constexpr uint32_t stage_bytes = Q::stage_payload + 16;  // one spare 16-byte group for the funnel read
     static constexpr uint32_t out_buf_bytes = Q::out_bytes + 16;  // room for a spill word
     // per-warp layout
     static constexpr uint32_t off_bar = 0;
@@ -120,12 +143,32 @@ struct StreamCfg : ChunkGeom<N_, SYN, G> {
     static_assert(!INPLACE || S >= 2, "in-place refills lag one iteration");
 };
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE>
+// Load chunk c into a stage; called by every lane of the warp.  Unpadded
+// stages: lane 0 issues one bulk copy.  Padded: lane 0 announces the bytes,
+// then every lane copies its own part into its slot.
+template <class Cfg, bool XH>
+__device__ __forceinline__ void issue_chunk(const uint32_t *in, uint64_t c, uint8_t *stage, uint64_t *bar, int lane)
+{
+    if constexpr (!Cfg::PADDED) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, Cfg::in_bytes);
+            bulk_g2s(stage, in + c * (uint64_t)Cfg::in_words, Cfg::in_bytes, bar);
+        }
+    } else {
+        if (lane == 0) mbar_arrive_expect_tx(bar, Cfg::in_bytes);
+        __syncwarp();
+        bulk_g2s(stage + lane * Cfg::part_words * 4, in + c * (uint64_t)Cfg::in_words + (uint64_t)lane * Cfg::R,
+                 Cfg::R * 4, bar);
+    }
+}
+
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
 __global__ void __launch_bounds__(T)
     k_decode_stream(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint8_t *__restrict__ syn,
-                    unsigned long long *__restrict__ err, uint32_t *__restrict__ status, uint64_t nchunks)
+                    unsigned long long *__restrict__ err, uint32_t *__restrict__ status, uint64_t nchunks,
+                    unsigned long long *__restrict__ det)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * Cfg::warp_bytes;
@@ -136,22 +179,36 @@ __global__ void __launch_bounds__(T)
     const uint64_t gw = (uint64_t)blockIdx.x * Cfg::WARPS + warp;  // global warp index
     const uint64_t tw = (uint64_t)gridDim.x * Cfg::WARPS;          // warps in the grid
 
-    if (lane == 0) {
+    if constexpr (!Cfg::PADDED) {
+        if (lane == 0) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
+            for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+            fence_mbar_init();
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const uint64_t c = gw + (uint64_t)s * tw;
+                if (c < nchunks) {
+                    mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
+                    bulk_g2s(s_in + s * Cfg::stage_bytes, in + c * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
+                }
+            }
+        }
+    } else {
+        if (lane == 0) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+            fence_mbar_init();
+        }
+        __syncwarp();  // every lane's copies complete on the barriers
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const uint64_t c = gw + (uint64_t)s * tw;
-            if (c < nchunks) {
-                mbar_arrive_expect_tx(&bar[s], Cfg::in_bytes);
-                bulk_g2s(s_in + s * Cfg::stage_bytes, in + c * (uint64_t)Cfg::in_words, Cfg::in_bytes, &bar[s]);
-            }
+            if (c < nchunks) issue_chunk<Cfg, true>(in, c, s_in + s * Cfg::stage_bytes, &bar[s], lane);
         }
     }
     __syncwarp();
 
-    uint32_t errs = 0;
+    uint32_t errs = 0, dets = 0;
     uint32_t it = 0;
     bool aborted = false;
     for (uint64_t c = gw; c < nchunks; c += tw, ++it) {
@@ -170,10 +227,31 @@ __global__ void __launch_bounds__(T)
         const uint32_t *stage = reinterpret_cast<const uint32_t *>(s_in + s * Cfg::stage_bytes);
         uint32_t *obase = INPLACE ? reinterpret_cast<uint32_t *>(s_in + s * Cfg::stage_bytes)
                                   : reinterpret_cast<uint32_t *>(s_out + ob * Cfg::out_buf_bytes);
-        errs += decode_warp_chunk<N_, SYN, G>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane);
+        errs += decode_warp_chunk<N_, SYN, G, XH>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane, dets);
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
+        if constexpr (Cfg::PADDED) {
+            if constexpr (INPLACE) {
+                if (lane == 0) bulk_wait_read<0>();  // last iteration's store has read its stage
+                __syncwarp();
+                if (it > 0) {
+                    const uint64_t cn = c - tw + (uint64_t)S * tw;
+                    if (cn < nchunks)
+                        issue_chunk<Cfg, true>(in, cn, s_in + (int)((it - 1) % S) * Cfg::stage_bytes,
+                                               &bar[(it - 1) % S], lane);
+                }
+            }
+            if (lane == 0) {
+                bulk_s2g(out + c * (uint64_t)Cfg::out_words, obase, Cfg::out_bytes);
+                if constexpr (SYN != 0)
+                    bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
+                bulk_commit();
+            }
+            if constexpr (!INPLACE) {
+                const uint64_t cn = c + (uint64_t)S * tw;
+                if (cn < nchunks) issue_chunk<Cfg, true>(in, cn, s_in + s * Cfg::stage_bytes, &bar[s], lane);
+            }
+        } else if (lane == 0) {
             if constexpr (INPLACE) {
                 // the store issued last iteration has finished reading its stage: refill that
                 // stage with the chunk S iterations after it (so in place the lookahead is S - 1)
@@ -221,36 +299,45 @@ __global__ void __launch_bounds__(T)
         for (int o = 16; o > 0; o >>= 1) errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
         if (lane == 0 && errs != 0) atomicAdd(err, (unsigned long long)errs);
     }
+    if constexpr (XH) {
+        if (det != nullptr) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dets += __shfl_xor_sync(0xFFFFFFFFu, dets, o);
+            if (lane == 0 && dets != 0) atomicAdd(det, (unsigned long long)dets);
+        }
+    }
 }
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
-                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st);
+                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
+                                  unsigned long long *det);
 
 // Per-device configuration of a kernel (dynamic shared memory opt-in and the
 // number of resident CTAs per SM).
 int stream_blocks_per_sm(const void *kernel, int threads, uint32_t smem);
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
-                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st)
+                                  void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
+                                  unsigned long long *det)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
-    auto kern = k_decode_stream<N_, SYN, T, S, G, INPLACE>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
+    auto kern = k_decode_stream<N_, SYN, T, S, G, INPLACE, XH>;
     const int bps = stream_blocks_per_sm(reinterpret_cast<const void *>(kern), T, Cfg::smem);
     if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
     const int grid = (int)(want < cap ? want : cap);
-    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks);
+    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det);
     count_launch();
     return cudaGetLastError();
 }
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
 StreamVariant make_variant()
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
     StreamVariant v;
     v.n = N_;
     v.syn = SYN;
@@ -260,18 +347,19 @@ StreamVariant make_variant()
     v.inplace = INPLACE;
     v.smem = Cfg::smem;
     v.chunk_cw = (uint64_t)32 * G;
-    v.launch = &launch_stream_variant<N_, SYN, T, S, G, INPLACE>;
-    v.kernel = reinterpret_cast<const void *>(k_decode_stream<N_, SYN, T, S, G, INPLACE>);
+    v.launch = &launch_stream_variant<N_, SYN, T, S, G, INPLACE, XH>;
+    v.kernel = reinterpret_cast<const void *>(k_decode_stream<N_, SYN, T, S, G, INPLACE, XH>);
+    v.xh = XH ? 1 : 0;
     return v;
 }
 
 // All syndrome types of one configuration.
-template <int N_, int T, int S, int G, int INPLACE>
+template <int N_, int T, int S, int G, int INPLACE, bool XH = false>
 void add_variants(std::vector<StreamVariant> &out)
 {
-    out.push_back(make_variant<N_, 0, T, S, G, INPLACE>());
-    out.push_back(make_variant<N_, 1, T, S, G, INPLACE>());
-    out.push_back(make_variant<N_, 2, T, S, G, INPLACE>());
+    out.push_back(make_variant<N_, 0, T, S, G, INPLACE, XH>());
+    out.push_back(make_variant<N_, 1, T, S, G, INPLACE, XH>());
+    out.push_back(make_variant<N_, 2, T, S, G, INPLACE, XH>());
 }
 
 }  // namespace hd

@@ -231,6 +231,26 @@ __device__ __forceinline__ uint32_t part_y(const uint32_t (&r)[R], int c, int w)
     return __funnelshift_r(r[a], hi, sh);
 }
 
+// SECDED (XH): codeword c occupies bits [c*(n+1), (c+1)*(n+1)) of the part and
+// position p is its bit p, so its words are the position domain directly
+// (position 0 is the overall parity bit); shorter codewords are masked.
+template <int N_, int R>
+__device__ __forceinline__ uint32_t part_y_xh(const uint32_t (&r)[R], int c, int w)
+{
+    constexpr int L = N_ + 1;
+    const int start = c * L + 32 * w;
+    const int a = start >> 5, sh = start & 31;
+    uint32_t v;
+    if (sh == 0) {
+        v = r[a];
+    } else {
+        const uint32_t hi = (a + 1 < R) ? r[a + 1] : 0u;
+        v = __funnelshift_r(r[a], hi, sh);
+    }
+    if constexpr (L < 32) v &= (1u << L) - 1u;
+    return v;
+}
+
 template <int N_>
 __device__ __forceinline__ uint32_t part_syndrome(const uint32_t (&y)[Code<N_>::Wy])
 {
@@ -258,16 +278,20 @@ __device__ __forceinline__ uint32_t part_syndrome(const uint32_t (&y)[Code<N_>::
 }
 
 // Decode the G codewords of a part held in r[] (bit 0 of r[0] is position 1
-// of its first codeword), appending data bits to `op` and syndromes to `sp`.
-template <int N_, int G, int R, class OP, class SP>
-__device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &sp)
+// of its first codeword, or position 0 with XH), appending data bits to `op`
+// and syndromes to `sp`.  XH (SECDED): the overall parity P of the n + 1 bits
+// decides the correction (P = 1: flip position s; P = 0: flip nothing, and
+// s != 0 is a detected double error, counted in `det`); the syndrome value is
+// s | P << m.
+template <int N_, int G, int R, bool XH = false, class OP, class SP>
+__device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &sp, uint32_t &det)
 {
     using C = Code<N_>;
 #pragma unroll
     for (int c = 0; c < G; ++c) {
         uint32_t y[C::Wy];
 #pragma unroll
-        for (int w = 0; w < C::Wy; ++w) y[w] = part_y<N_, R>(r, c, w);
+        for (int w = 0; w < C::Wy; ++w) y[w] = XH ? part_y_xh<N_, R>(r, c, w) : part_y<N_, R>(r, c, w);
         if constexpr (C::Wy == 1) {
             // checksum: parities of y & I_i, summed into fields, gathered into
             // the top m bits of st
@@ -277,18 +301,35 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
             for (int i = 1; i < C::m; ++i) pf = fma_lo(__popc(y[0] & qmask(N_, i)), 1u << (SG::F * i), pf);
             const uint32_t st = (pf & SG::lsbs()) * SG::mult();
             const uint32_t s = fma_hi(st, 1u << C::m, 0u);  // st >> (32 - m)
-            // correction: flip position s (s = 0 flips the unused bit 0)
-            y[0] ^= 1u << s;
+            // correction: flip position s (s = 0 flips bit 0, which is no data position)
+            if constexpr (XH) {
+                const uint32_t P = __popc(y[0]) & 1u;
+                y[0] ^= P << s;
+                det += (P == 0u && s != 0u) ? 1u : 0u;
+                sp.put(c, s | (P << C::m));
+            } else {
+                y[0] ^= 1u << s;
+            }
             // redundancy removal: run j moves down by j + 2 bits (high product)
             uint32_t d = 0;
 #pragma unroll
             for (int j = 1; j < C::m; ++j) d = fma_hi(y[0] & (run_mask(j) << (j + 2)), 1u << (30 - j), d);
             op.append(d, C::k);
-            sp.put(c, s);
+            if constexpr (!XH) sp.put(c, s);
         } else {
             const uint32_t s = part_syndrome<N_>(y);
+            uint32_t sf = s;  // the position to flip; past every word when nothing is flipped
+            if constexpr (XH) {
+                uint32_t f = 0;
 #pragma unroll
-            for (int w = 0; w < C::Wy; ++w) y[w] ^= shl_clamp(1u, s - 32u * (uint32_t)w);
+                for (int w = 0; w < C::Wy; ++w) f ^= y[w];
+                const uint32_t P = __popc(f) & 1u;
+                sf = P ? s : 0xFFFFFFFFu;
+                det += (P == 0u && s != 0u) ? 1u : 0u;
+                sp.put(c, s | (P << C::m));
+            }
+#pragma unroll
+            for (int w = 0; w < C::Wy; ++w) y[w] ^= shl_clamp(1u, sf - 32u * (uint32_t)w);
             uint32_t d0 = 0;
 #pragma unroll
             for (int j = 1; j < 5; ++j) d0 |= (y[0] >> (j + 2)) & run_mask(j);
@@ -300,7 +341,7 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
                 else
                     op.append(y[w], 32);
             }
-            sp.put(c, s);
+            if constexpr (!XH) sp.put(c, s);
         }
     }
     op.finish();

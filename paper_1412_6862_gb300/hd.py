@@ -123,6 +123,8 @@ SIGNATURES = {
     "hd_short_variant_count": (_i32, [_c.POINTER(_u32)]),
     "hd_short_variant_select": (_i32, [_c.c_int32]),
     "hd_short_autotune": (_i32, [_u32, _u64, _u32, _vp, _c.POINTER(_c.c_int32)]),
+    "hd_decode_secded": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "hd_encode_secded": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -516,6 +518,47 @@ def encode_short(data_words, n: int, num_codewords: int, out=None, cuda_stream=N
         out = torch.empty(max(4, words_for(num_codewords * n)), dtype=torch.int32, device=data_words.device)
     check(hd_encode_short(_ptr(data_words), n, num_codewords, _ptr(out), _stream_handle(cuda_stream)),
           "hd_encode_short")
+    return out
+
+
+def hd_decode_secded(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, detected_count,
+                     cuda_stream) -> int:
+    return lib().hd_decode_secded(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
+                                  detected_count, cuda_stream)
+
+
+def hd_encode_secded(data_bits, n, num_codewords, stream, cuda_stream) -> int:
+    return lib().hd_encode_secded(data_bits, n, num_codewords, stream, cuda_stream)
+
+
+def decode_secded(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U16, out=None, syndromes=None,
+                  counts=None, cuda_stream=None):
+    """Decode a device tensor of SECDED codewords (n + 1 bits each).  Returns
+    (out_words, syndromes or None, counts) with counts = [nonzero syndromes, detected]."""
+    import torch
+    m, k = code_params(n)
+    dev = stream_words.device
+    if out is None:
+        out = torch.empty(max(4, words_for(num_codewords * k)), dtype=torch.int32, device=dev)
+    if syndromes is None and syn_type != SYN_NONE:
+        dt = torch.uint8 if syn_type == SYN_U8 else torch.int16
+        syndromes = torch.empty(max(16, num_codewords), dtype=dt, device=dev)
+    if counts is None:
+        counts = torch.empty(2, dtype=torch.int64, device=dev)
+    rc = hd_decode_secded(_ptr(stream_words), (n + 1) * num_codewords, n, num_codewords, _ptr(out),
+                          _ptr(syndromes) if syn_type != SYN_NONE else None, syn_type, _ptr(counts),
+                          _ptr(counts) + 8, _stream_handle(cuda_stream))
+    check(rc, "hd_decode_secded")
+    return out, syndromes, counts
+
+
+def encode_secded(data_words, n: int, num_codewords: int, out=None, cuda_stream=None):
+    """Encode a device tensor of packed messages into SECDED codewords."""
+    import torch
+    if out is None:
+        out = torch.empty(max(4, words_for(num_codewords * (n + 1))), dtype=torch.int32, device=data_words.device)
+    check(hd_encode_secded(_ptr(data_words), n, num_codewords, _ptr(out), _stream_handle(cuda_stream)),
+          "hd_encode_secded")
     return out
 
 

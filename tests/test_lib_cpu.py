@@ -140,3 +140,16 @@ def test_short_host_side_validation(lib):
     assert hd.hd_encode_short(16, 11, 4, 20, None) == hd.HD_ERR_ALIGN
     assert hd.hd_short_variant_count() >= 1
     assert lib.hd_short_variant_select(hd.hd_short_variant_count()) == hd.HD_ERR_INVALID_ARG
+
+
+def test_secded_host_side_validation(lib):
+    assert hd.hd_decode_secded(16, 10 * 4, 9, 4, 16, None, 0, None, None, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode_secded(16, 7 * 4, 7, 4, 16, None, 0, None, None, None) == hd.HD_ERR_SIZE  # needs 8 * 4
+    assert hd.hd_decode_secded(None, 8 * 4, 7, 4, 16, None, 0, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_secded(16, 8 * 4, 7, 4, None, None, 0, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_secded(20, 8 * 4, 7, 4, 16, None, 0, None, None, None) == hd.HD_ERR_ALIGN
+    assert hd.hd_decode_secded(16, 256 * 4, 255, 4, 16, 32, hd.SYN_U8, None, None, None) == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_secded(16, 128 * 4, 127, 4, 16, None, hd.SYN_U8, None, None, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_secded(None, 0, 63, 0, None, None, 0, None, None, None) == hd.HD_OK
+    assert hd.hd_encode_secded(16, 9, 4, 16, None) == hd.HD_ERR_INVALID_N
+    assert hd.hd_encode_secded(None, 7, 4, 16, None) == hd.HD_ERR_NULL

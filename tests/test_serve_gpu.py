@@ -88,3 +88,23 @@ def test_server_submit_poll_drain_and_budget():
     assert srv.submit(big["d_in"].data_ptr(), big["out"].data_ptr(), 0, huge_N, 7, 0, 1) == hd.HD_ERR_CAPACITY
     assert srv.submit(big["d_in"].data_ptr(), big["out"].data_ptr(), 0, 10, 8, 0, 1) == hd.HD_ERR_INVALID_N
     srv.close()
+
+
+def test_drain_waits_for_every_admitted_packet():
+    # admission moves requests out of the queue and marks their wave busy atomically, so a
+    # drain that returns HD_OK has every completion ready to poll (repeated to give a race
+    # between admission and drain many chances)
+    pk = _mixed(24, seed=13)
+    for rep in range(25):
+        srv = hd.Server(hd.server_config(max_waves=3, max_wave_packets=4, max_wave_tiles=4096, queue_capacity=256,
+                                         mem_cap_bytes=1 << 34))
+        try:
+            for j, p in enumerate(pk):
+                assert srv.submit(p["d_in"].data_ptr(), p["out"].data_ptr(),
+                                  0 if p["syn"] is None else p["syn"].data_ptr(), p["N"], p["n"], p["st"],
+                                  j) == hd.HD_OK
+            assert srv.drain(60.0) == hd.HD_OK
+            rc, comps = srv.poll(1000)
+            assert rc == hd.HD_OK and len(comps) == len(pk), (rep, len(comps))
+        finally:
+            srv.close()
