@@ -744,13 +744,15 @@ def run_ours(args):
     h2d = sum(bufs[n]["pinned"].numel() * 4 for n in codes)
     d2h = sum(bufs[n]["out"].numel() * 4 + bufs[n]["syn"].numel() + 8 for n in codes)
 
+    e2e_jobs = [(bufs[n]["pinned"].data_ptr(), n, bufs[n]["N"], bufs[n]["out_h"].data_ptr(),
+                 bufs[n]["syn_h"].data_ptr(), hd.SYN_U8) for n in codes]
+
     def e2e_step():
-        for n in codes:
-            b = bufs[n]
-            rc, _ = hd.hd_decode_host(b["pinned"].data_ptr(), n * b["N"], n, b["N"], b["out_h"].data_ptr(),
-                                      b["syn_h"].data_ptr(), hd.SYN_U8, 0, 0)
-            if rc != 0:
-                raise hd.HDError(rc, "hd_decode_host")
+        # the three streams in one pipeline of host-to-device copies, decodes and
+        # device-to-host copies (one fill and one drain per step)
+        rc, _ = hd.hd_decode_host_batch(e2e_jobs)
+        if rc != 0:
+            raise hd.HDError(rc, "hd_decode_host_batch")
 
     e2e_steps = 0 if args.no_e2e else args.e2e_steps
     for _ in range(3 if e2e_steps else 0):

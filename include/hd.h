@@ -77,7 +77,7 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
 
 /* Decode from and to HOST memory with overlapped transfers -- the paper's
  * asynchronous data transfer (Sec. III-B, Fig. 5, Eq. 1).  The stream is cut
- * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^20) and each
+ * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^21) and each
  * chunk's host-to-device copy, decode and device-to-host copy run on one of
  * `depth` CUDA streams (0 = 4, at most 8), so copies in both directions
  * overlap with the decoding of neighbouring chunks.  Arguments and results are
@@ -90,6 +90,27 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
 hd_status hd_decode_host(const uint32_t *host_stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
                          uint32_t *host_out, void *host_syndromes, hd_syn_type syn_type,
                          unsigned long long *host_err_count, uint64_t chunk_codewords, uint32_t depth);
+
+/* Several host-buffer decodes in one pipeline (the same asynchronous data
+ * transfer as hd_decode_host, without a fill and drain per stream).  Each job
+ * names a host stream of num_codewords codewords of length n and its host
+ * outputs, as the arguments of hd_decode_host (pinned memory for overlap);
+ * *host_err_count (or NULL) receives the job's number of nonzero syndromes.
+ * All jobs' chunks (chunk_codewords, a multiple of 128; 0 = 2^21) go through
+ * `depth` rotating CUDA streams (0 = 4, at most 8); the first chunks of the
+ * batch ramp up from chunk/8 and the last ones ramp down, so the pipeline
+ * fills and drains on small copies.  Synchronous; errors as hd_decode_host. */
+typedef struct {
+    const uint32_t *host_stream;
+    uint32_t *host_out;
+    void *host_syndromes;
+    unsigned long long *host_err_count;
+    uint64_t num_codewords;
+    uint32_t n;
+    uint32_t syn_type; /* an hd_syn_type */
+} hd_host_job;
+
+hd_status hd_decode_host_batch(const hd_host_job *jobs, uint32_t num_jobs, uint64_t chunk_codewords, uint32_t depth);
 
 /* Encode `num_codewords` messages (the transmitter side of Sec. II: the
  * checksum bits are added to the message).  data_bits holds message i at bits

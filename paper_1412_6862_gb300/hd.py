@@ -63,6 +63,12 @@ class PlanInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class HostJob(ctypes.Structure):
+    _fields_ = [("host_stream", _c.c_void_p), ("host_out", _c.c_void_p), ("host_syndromes", _c.c_void_p),
+                ("host_err_count", _c.c_void_p), ("num_codewords", _c.c_uint64), ("n", _c.c_uint32),
+                ("syn_type", _c.c_uint32)]
+
+
 class ServerConfig(ctypes.Structure):
     """Mirror of hd_server_config."""
     _fields_ = [("max_waves", _u32), ("max_wave_packets", _u32), ("max_wave_tiles", _u32),
@@ -125,6 +131,7 @@ SIGNATURES = {
     "hd_short_autotune": (_i32, [_u32, _u64, _u32, _vp, _c.POINTER(_c.c_int32)]),
     "hd_decode_secded": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp, _vp]),
     "hd_encode_secded": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_decode_host_batch": (_i32, [_c.POINTER(HostJob), _u32, _u64, _u32]),
     "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
@@ -189,6 +196,17 @@ def hd_decode_host(host_stream, in_bits, n, num_codewords, host_out, host_syndro
     rc = lib().hd_decode_host(host_stream, in_bits, n, num_codewords, host_out, host_syndromes, syn_type,
                               ctypes.byref(err), chunk_codewords, depth)
     return rc, int(err.value)
+
+
+def hd_decode_host_batch(jobs, chunk_codewords: int = 0, depth: int = 0):
+    """jobs: list of (host_stream_ptr, n, num_codewords, host_out_ptr, host_syn_ptr or None, syn_type).
+    Returns (status, [err_count per job])."""
+    arr = (HostJob * max(1, len(jobs)))()
+    errs = (_c.c_ulonglong * max(1, len(jobs)))()
+    for i, (hs, n, N, ho, hsyn, st) in enumerate(jobs):
+        arr[i] = HostJob(hs, ho, hsyn, ctypes.addressof(errs) + 8 * i, N, n, st)
+    rc = lib().hd_decode_host_batch(arr, len(jobs), chunk_codewords, depth)
+    return rc, [int(errs[i]) for i in range(len(jobs))]
 
 
 def decode_host(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U8, out=None, syndromes=None,

@@ -4,6 +4,8 @@ CUDA call."""
 import ctypes
 import shutil
 
+import numpy as np
+
 import pytest
 
 from paper_1412_6862_gb300 import build as hd_build
@@ -153,3 +155,15 @@ def test_secded_host_side_validation(lib):
     assert hd.hd_decode_secded(None, 0, 63, 0, None, None, 0, None, None, None) == hd.HD_OK
     assert hd.hd_encode_secded(16, 9, 4, 16, None) == hd.HD_ERR_INVALID_N
     assert hd.hd_encode_secded(None, 7, 4, 16, None) == hd.HD_ERR_NULL
+
+
+def test_host_batch_validation_host_only(lib):
+    z = np.zeros(64, np.uint32)
+    good = (z.ctypes.data, 15, 4, z.ctypes.data, None, 0)
+    assert hd.hd_decode_host_batch([])[0] == hd.HD_OK
+    assert hd.hd_decode_host_batch([good, (z.ctypes.data, 14, 4, z.ctypes.data, None, 0)])[0] == hd.HD_ERR_INVALID_N
+    assert hd.hd_decode_host_batch([good], 100, 0)[0] == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_host_batch([good], 0, 9)[0] == hd.HD_ERR_INVALID_ARG
+    assert hd.hd_decode_host_batch([(None, 15, 4, z.ctypes.data, None, 0)])[0] == hd.HD_ERR_NULL
+    assert hd.hd_decode_host_batch([(z.ctypes.data, 15, 4, z.ctypes.data, None, 1)])[0] == hd.HD_ERR_NULL
+    assert lib.hd_decode_host_batch(None, 1, 0, 0) == hd.HD_ERR_NULL
