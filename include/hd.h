@@ -70,7 +70,12 @@ typedef enum {
  *               number of codewords whose syndrome is nonzero.
  * Two errors in one codeword give syndrome p XOR q and the decoder flips that
  * third position, as any single-error-correcting Hamming decoder does.
- * num_codewords == 0 is HD_OK; it only zeroes *err_count. */
+ * num_codewords == 0 is HD_OK; it only zeroes *err_count.
+ * For n = 7 and 15 the chosen configuration may decode through a table of
+ * 2^n entries (data bits and syndrome per codeword value) kept in static
+ * device memory; the first such call on a device fills it with a kernel on
+ * `cuda_stream` and synchronises that stream (a first call inside a stream
+ * capture uses the arithmetic decoder instead). */
 hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
                     uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
                     unsigned long long *err_count, void *cuda_stream);
@@ -231,6 +236,8 @@ typedef struct {
     uint64_t chunk_codewords;      /* codewords per CTA iteration */
     int32_t blocks_per_sm;         /* resident CTAs per SM on the current device */
     float measured_us;             /* autotuner time of the request, -1 when not measured */
+    uint32_t table_lookup;         /* 1: decodes by one shared-memory table lookup per codeword (n = 7, 15);
+                                      the table (2^n 16-bit entries) is filled on first use, see hd_decode() */
 } hd_variant_info;
 
 /* Number of compiled configurations for (n, syn_type).  Host only. */

@@ -60,22 +60,26 @@ std::map<std::tuple<int, uint32_t, int>, int> g_choice;
 // device -> address of g_hd_status
 std::map<int, uint32_t *> g_status_ptr;
 
-// Built-in choice per (n, G, T, S, inplace), measured on GB300; used until the
-// autotuner or the caller picks another configuration.
+// Built-in choice per (n, G, T, S, inplace, decode table), measured on GB300;
+// used until the autotuner or the caller picks another configuration.  The
+// first entry of n that is compiled for the syndrome type wins (the 576-thread
+// n = 15 configuration has no u16-syndrome build: its buffers exceed a CTA's
+// shared memory).
 struct DefaultCfg {
     uint32_t n;
-    int G, T, S, inplace;
+    int G, T, S, inplace, lut;
 };
 constexpr DefaultCfg kDefaults[] = {
-    {7, 32, 128, 4, 1},  {15, 32, 512, 2, 1}, {31, 32, 128, 4, 1},
-    {63, 32, 128, 2, 1}, {127, 8, 256, 3, 1}, {255, 8, 128, 2, 1},
+    {7, 32, 128, 4, 1, 1},  {15, 32, 576, 2, 0, 1}, {15, 32, 512, 2, 1, 1}, {31, 32, 128, 3, 1, 0},
+    {63, 32, 128, 3, 1, 0}, {127, 8, 256, 3, 1, 0}, {255, 8, 128, 2, 1, 0},
 };
 
-int find_variant(uint32_t n, int syn, int G, int T, int S, int inplace)
+int find_variant(uint32_t n, int syn, int G, int T, int S, int inplace, int lut)
 {
     const auto &v = variants();
     for (size_t i = 0; i < v.size(); ++i)
-        if (v[i].n == n && v[i].syn == syn && v[i].G == G && v[i].T == T && v[i].S == S && v[i].inplace == inplace)
+        if (v[i].n == n && v[i].syn == syn && v[i].G == G && v[i].T == T && v[i].S == S &&
+            v[i].inplace == inplace && v[i].lut == lut)
             return (int)i;
     return -1;
 }
@@ -84,7 +88,7 @@ int default_variant(uint32_t n, int syn)
 {
     for (const auto &d : kDefaults)
         if (d.n == n) {
-            const int i = find_variant(n, syn, d.G, d.T, d.S, d.inplace);
+            const int i = find_variant(n, syn, d.G, d.T, d.S, d.inplace, d.lut);
             if (i >= 0) return i;
         }
     const auto &v = variants();
@@ -150,8 +154,13 @@ cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, 
     if (nchunks == 0) return cudaSuccess;
     uint32_t *status = status_ptr();
     if (status == nullptr) return cudaErrorInvalidSymbol;
+    const uint16_t *lut = nullptr;
+    if (v.lut) {
+        lut = lut_ptr(n, st);
+        if (lut == nullptr) return cudaSuccess;  // no table yet (first call inside a capture): generic path
+    }
     *covered = nchunks * v.chunk_cw;
-    return v.launch(v, in, nchunks, out, syn, err, status, st, nullptr);
+    return v.launch(v, in, nchunks, out, syn, err, status, st, nullptr, lut);
 }
 
 // SECDED: the streaming kernel with codewords of n + 1 bits, compiled in the
@@ -170,7 +179,7 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
     uint32_t *status = status_ptr();
     if (status == nullptr) return cudaErrorInvalidSymbol;
     *covered = nchunks * v->chunk_cw;
-    return v->launch(*v, in, nchunks, out, syn, err, status, st, det);
+    return v->launch(*v, in, nchunks, out, syn, err, status, st, det, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,6 +200,7 @@ static void fill_info(int idx, hd_variant_info *info)
     info->chunk_codewords = v.chunk_cw;
     info->blocks_per_sm = stream_blocks_per_sm(v.kernel, v.T, v.smem);
     info->measured_us = -1.0f;
+    info->table_lookup = (uint32_t)v.lut;
 }
 
 }  // namespace hd
@@ -303,15 +313,17 @@ hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, 
         if (stream_blocks_per_sm(v.kernel, v.T, v.smem) <= 0) continue;
         void *sy = syn_type == HD_SYN_NONE ? nullptr : dsyn;
         auto *er = static_cast<unsigned long long *>(derr);
+        const uint16_t *lut = v.lut ? lut_ptr(n, st) : nullptr;
+        if (v.lut && lut == nullptr) continue;
         if (v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status,
-                     st, nullptr) != cudaSuccess) {
+                     st, nullptr, lut) != cudaSuccess) {
             rc = HD_ERR_CUDA;
             break;
         }
         cudaEventRecord(e0, st);
         for (uint32_t r = 0; r < reps; ++r)
             v.launch(v, static_cast<const uint32_t *>(din), nchunks, static_cast<uint32_t *>(dout), sy, er, status, st,
-                     nullptr);
+                     nullptr, lut);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = HD_ERR_CUDA;

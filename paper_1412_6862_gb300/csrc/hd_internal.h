@@ -47,6 +47,11 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
                                       int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
                                       uint64_t *covered);
 
+// Decode table of n = 7 or 15 (data | s << k per codeword), filled on `st` on
+// first use per device; nullptr for other n, or when the table is not filled
+// yet and `st` is capturing.
+const uint16_t *lut_ptr(uint32_t n, cudaStream_t st);
+
 // Device address of the status word that kernels latch HD_ERR_TIMEOUT into
 // (per device; nullptr on failure), and its host-side read-and-clear.
 uint32_t *status_ptr();

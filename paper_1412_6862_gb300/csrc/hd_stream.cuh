@@ -35,9 +35,11 @@ struct StreamVariant {
     uint32_t smem;
     uint64_t chunk_cw;  // codewords per warp iteration (32*G)
     cudaError_t (*launch)(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out, void *syn,
-                          unsigned long long *err, uint32_t *status, cudaStream_t st, unsigned long long *det);
+                          unsigned long long *err, uint32_t *status, cudaStream_t st, unsigned long long *det,
+                          const uint16_t *lut);
     const void *kernel;
-    int xh = 0;  // SECDED: codewords of n + 1 bits with the overall parity bit at position 0
+    int xh = 0;   // SECDED: codewords of n + 1 bits with the overall parity bit at position 0
+    int lut = 0;  // decode table (n = 7, 15): one shared-memory lookup per codeword
 };
 
 // Geometry of one warp chunk of code n: 32*G codewords, G tiles of 32.  XH:
@@ -79,9 +81,9 @@ struct ChunkGeom {
 // equal `stage`: every lane copies its part to registers and the warp
 // synchronises before the first write) and its syndromes at `sbase`.  Returns
 // this lane's count of nonzero syndromes.
-template <int N_, int SYN, int G, bool XH = false>
+template <int N_, int SYN, int G, bool XH = false, bool LUT = false>
 __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uint32_t *obase, uint8_t *sbase, int lane,
-                                                      uint32_t &det)
+                                                      uint32_t &det, const uint16_t *lut = nullptr)
 {
     using Q = ChunkGeom<N_, SYN, G, XH>;
     constexpr int H = Q::H;
@@ -116,7 +118,7 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
     __syncwarp();  // the whole chunk is in registers
     OutPacker<Q::GK, Q::ALIGNED, Q::V> op(obase + out_w, out_sh);
     SynPacker<Q::SB, SYN != 0, G, Q::WIDE> sp(sbase + (uint32_t)lane * G * Q::SB);
-    decode_part<N_, G, Q::R, XH>(r, op, sp, det);
+    decode_part<N_, G, Q::R, XH, LUT>(r, op, sp, det, lut);
     return sp.nonzero();
 }
 
@@ -124,7 +126,7 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
 // mbarrier each, (unless INPLACE) two output staging buffers, and two syndrome
 // buffers.  Lane 0 issues the warp's bulk loads and stores; warps never wait
 // for one another, so one warp's memory wait overlaps the others' arithmetic.
-template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     using Q = ChunkGeom<N_, SYN, G, XH>;
     static constexpr int WARPS = T / 32;
@@ -136,9 +138,11 @@ struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     static constexpr uint32_t off_out = off_in + S * stage_bytes;
     static constexpr uint32_t off_syn = off_out + (INPLACE ? 0 : 2 * out_buf_bytes);
     static constexpr uint32_t warp_bytes = (off_syn + 2 * Q::syn_bytes + 127) / 128 * 128;
-    static constexpr uint32_t smem = WARPS * warp_bytes;
+    static constexpr uint32_t lut_bytes = LUT ? (2u << N_) : 0u;  // u16 per codeword value
+    static constexpr uint32_t off_lut = WARPS * warp_bytes;         // the table, then its mbarrier
+    static constexpr uint32_t smem = off_lut + (LUT ? lut_bytes + 16u : 0u);
+    static constexpr bool fits = smem <= 232448;  // the opt-in maximum per CTA
     static_assert(T % 32 == 0 && S <= 8, "whole warps, at most 8 stages");
-    static_assert(smem <= 232448, "shared memory per CTA");
     static_assert(!INPLACE || Q::out_bytes + 16 <= stage_bytes, "in-place output fits the input stage");
     static_assert(!INPLACE || S >= 2, "in-place refills lag one iteration");
 };
@@ -162,15 +166,33 @@ __device__ __forceinline__ void issue_chunk(const uint32_t *in, uint64_t c, uint
     }
 }
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 __global__ void __launch_bounds__(T)
     k_decode_stream(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint8_t *__restrict__ syn,
                     unsigned long long *__restrict__ err, uint32_t *__restrict__ status, uint64_t nchunks,
-                    unsigned long long *__restrict__ det)
+                    unsigned long long *__restrict__ det, const uint16_t *__restrict__ lut)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *lut_bar = nullptr;
+    if constexpr (LUT) {
+        // the decode table: bulk copies into shared memory behind the warps'
+        // areas, in flight together with the warps' first chunks
+        static_assert(Cfg::lut_bytes % 16 == 0 && Cfg::off_lut % 16 == 0, "bulk copy granularity");
+        lut_bar = reinterpret_cast<uint64_t *>(smem + Cfg::off_lut + Cfg::lut_bytes);
+        if (threadIdx.x == 0) {
+            mbar_init(lut_bar, 1);
+            fence_mbar_init();
+            mbar_arrive_expect_tx(lut_bar, Cfg::lut_bytes);
+            constexpr uint32_t piece = Cfg::lut_bytes < 16384u ? Cfg::lut_bytes : 16384u;
+            static_assert(Cfg::lut_bytes % piece == 0, "whole pieces");
+#pragma unroll
+            for (uint32_t o = 0; o < Cfg::lut_bytes; o += piece)
+                bulk_g2s(smem + Cfg::off_lut + o, reinterpret_cast<const uint8_t *>(lut) + o, piece, lut_bar);
+        }
+        __syncthreads();  // the barrier is initialised before any thread waits on it
+    }
     uint8_t *wbase = smem + warp * Cfg::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
     uint8_t *s_in = wbase + Cfg::off_in;
@@ -211,7 +233,13 @@ __global__ void __launch_bounds__(T)
     uint32_t errs = 0, dets = 0;
     uint32_t it = 0;
     bool aborted = false;
-    for (uint64_t c = gw; c < nchunks; c += tw, ++it) {
+    const uint16_t *s_lut = nullptr;
+    if constexpr (LUT) {
+        const bool ok = mbar_wait_bounded(lut_bar, 0);
+        aborted = __any_sync(0xFFFFFFFFu, !ok);
+        s_lut = reinterpret_cast<const uint16_t *>(smem + Cfg::off_lut);
+    }
+    for (uint64_t c = gw; !aborted && c < nchunks; c += tw, ++it) {
         const int s = (int)(it % S);
         const uint32_t parity = (it / S) & 1u;
         const int ob = (int)(it & 1u);
@@ -227,7 +255,7 @@ __global__ void __launch_bounds__(T)
         const uint32_t *stage = reinterpret_cast<const uint32_t *>(s_in + s * Cfg::stage_bytes);
         uint32_t *obase = INPLACE ? reinterpret_cast<uint32_t *>(s_in + s * Cfg::stage_bytes)
                                   : reinterpret_cast<uint32_t *>(s_out + ob * Cfg::out_buf_bytes);
-        errs += decode_warp_chunk<N_, SYN, G, XH>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane, dets);
+        errs += decode_warp_chunk<N_, SYN, G, XH, LUT>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane, dets, s_lut);
         fence_proxy_async_smem();
         __syncwarp();
         if constexpr (Cfg::PADDED) {
@@ -285,12 +313,14 @@ __global__ void __launch_bounds__(T)
         if (aborted) {
             atomicOr(status, (uint32_t)HD_ERR_TIMEOUT);
             // wait (bounded) for every load still in flight into this warp's ring
-            // (in-place refills lag one iteration, so one fewer is outstanding)
-            const uint32_t pending = INPLACE ? S - 1 : S;
+            // (after the first iteration in-place refills lag one iteration, so
+            // one fewer is outstanding) and for the table
+            const uint32_t pending = (INPLACE && it > 0) ? S - 1 : S;
             for (uint32_t j = it; j < it + pending; ++j) {
                 const uint64_t cj = gw + (uint64_t)j * tw;
                 if (cj < nchunks) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
             }
+            if constexpr (LUT) (void)mbar_wait_bounded(lut_bar, 0);
         }
         bulk_wait_all<0>();
     }
@@ -308,36 +338,38 @@ __global__ void __launch_bounds__(T)
     }
 }
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
                                   void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
-                                  unsigned long long *det);
+                                  unsigned long long *det, const uint16_t *lut);
 
 // Per-device configuration of a kernel (dynamic shared memory opt-in and the
 // number of resident CTAs per SM).
 int stream_blocks_per_sm(const void *kernel, int threads, uint32_t smem);
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH, bool LUT>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
                                   void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
-                                  unsigned long long *det)
+                                  unsigned long long *det, const uint16_t *lut)
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
-    auto kern = k_decode_stream<N_, SYN, T, S, G, INPLACE, XH>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>;
+    if (LUT && lut == nullptr) return cudaErrorInvalidValue;
+    auto kern = k_decode_stream<N_, SYN, T, S, G, INPLACE, XH, LUT>;
     const int bps = stream_blocks_per_sm(reinterpret_cast<const void *>(kern), T, Cfg::smem);
     if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
     const int grid = (int)(want < cap ? want : cap);
-    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det);
+    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
     count_launch();
     return cudaGetLastError();
 }
 
-template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false>
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 StreamVariant make_variant()
 {
-    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH>;
+    using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>;
+    static_assert(Cfg::fits, "shared memory per CTA");
     StreamVariant v;
     v.n = N_;
     v.syn = SYN;
@@ -347,19 +379,29 @@ StreamVariant make_variant()
     v.inplace = INPLACE;
     v.smem = Cfg::smem;
     v.chunk_cw = (uint64_t)32 * G;
-    v.launch = &launch_stream_variant<N_, SYN, T, S, G, INPLACE, XH>;
-    v.kernel = reinterpret_cast<const void *>(k_decode_stream<N_, SYN, T, S, G, INPLACE, XH>);
+    v.launch = &launch_stream_variant<N_, SYN, T, S, G, INPLACE, XH, LUT>;
+    v.kernel = reinterpret_cast<const void *>(k_decode_stream<N_, SYN, T, S, G, INPLACE, XH, LUT>);
     v.xh = XH ? 1 : 0;
+    v.lut = LUT ? 1 : 0;
     return v;
 }
 
-// All syndrome types of one configuration.
-template <int N_, int T, int S, int G, int INPLACE, bool XH = false>
+// Every syndrome type of one configuration whose shared memory fits a CTA
+// (the u16 syndrome buffers are twice the u8 ones).
+template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH, bool LUT>
+void add_variant_if_fits(std::vector<StreamVariant> &out)
+{
+    if constexpr (StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>::fits)
+        out.push_back(make_variant<N_, SYN, T, S, G, INPLACE, XH, LUT>());
+}
+
+template <int N_, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 void add_variants(std::vector<StreamVariant> &out)
 {
-    out.push_back(make_variant<N_, 0, T, S, G, INPLACE, XH>());
-    out.push_back(make_variant<N_, 1, T, S, G, INPLACE, XH>());
-    out.push_back(make_variant<N_, 2, T, S, G, INPLACE, XH>());
+    static_assert(StreamCfg<N_, 0, T, S, G, INPLACE, XH, LUT>::fits, "shared memory per CTA");
+    add_variant_if_fits<N_, 0, T, S, G, INPLACE, XH, LUT>(out);
+    add_variant_if_fits<N_, 1, T, S, G, INPLACE, XH, LUT>(out);
+    add_variant_if_fits<N_, 2, T, S, G, INPLACE, XH, LUT>(out);
 }
 
 }  // namespace hd

@@ -31,9 +31,9 @@ __host__ __device__ constexpr uint32_t bmask(int i)
     return i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
-// Integer multiply-adds.  Multiplying by 2^t shifts left (mad.lo) or, keeping
-// the high word, shifts right by 32-t (mad.hi); adding bit fields that do not
-// overlap equals OR-ing them.  The compiler is free to issue these as shifts.
+// Integer multiply-add.  Multiplying by 2^t shifts left; adding bit fields
+// that do not overlap equals OR-ing them, so packing runs on the multiply pipe
+// beside the logic operations of the decoder.
 __device__ __forceinline__ uint32_t fma_lo(uint32_t a, uint32_t b, uint32_t c)
 {
     uint32_t d;
@@ -41,10 +41,30 @@ __device__ __forceinline__ uint32_t fma_lo(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
-__device__ __forceinline__ uint32_t fma_hi(uint32_t a, uint32_t b, uint32_t c)
+// Bits of a where K is set, else bits of b: one three-input logic operation
+// (truth table 0xCA = K ? a : b for the inputs K = 0xF0, a = 0xCC, b = 0xAA).
+__device__ __forceinline__ uint32_t bitsel(uint32_t K, uint32_t a, uint32_t b)
 {
-    uint32_t d;
-    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    uint32_t r;
+    asm("lop3.b32 %0, %1, %2, %3, 0xCA;" : "=r"(r) : "r"(K), "r"(a), "r"(b));
+    return r;
+}
+
+// Redundancy removal within one position-domain word (bit p = position p):
+// the data positions between the powers of two, run j = positions
+// 2^j + 1 .. 2^(j+1) - 1 for j = 1 .. M - 1 (M <= 5), move down by j + 2 bits
+// to data bits 0 ..  One shift by 3 moves every run; the remaining j - 1 bits
+// are taken in binary: runs 2 and 4 move down one more bit, then runs 3 and 4
+// two more, each step a select between the word and its shifted copy (the
+// runs kept in place and the destinations of the moved runs never overlap).
+// With M = 5 the result has no bits above the 26 data bits; for shorter codes
+// the bits above the k data bits are whatever followed in the word.
+template <int M>
+__device__ __forceinline__ uint32_t compress_runs(uint32_t y)
+{
+    uint32_t d = y >> 3;  // run 1 at bit 0, run 2 at 2..4, run 3 at 6..12, run 4 at 14..28
+    if constexpr (M >= 3) d = bitsel(0x00001FC1u, d, d >> 1);  // keep runs 1, 3; runs 2, 4 to 1..3, 13..27
+    if constexpr (M >= 4) d = bitsel(0x0000000Fu, d, d >> 2);  // keep runs 1, 2; runs 3, 4 to 4..10, 11..25
     return d;
 }
 
@@ -148,7 +168,7 @@ struct OutPacker {
             acc = fma_lo(v, 1u << pos, acc);  // acc | (v << pos)
         if (pos + len >= 32) {
             emit(acc);
-            acc = (pos + len > 32) ? fma_hi(v, 1u << pos, 0u) : 0u;  // v >> (32 - pos)
+            acc = (pos + len > 32) ? v >> (32 - pos) : 0u;
             pos = pos + len - 32;
         } else {
             pos += len;
@@ -263,10 +283,17 @@ __device__ __forceinline__ uint32_t part_syndrome(const uint32_t (&y)[Code<N_>::
         uint32_t f = 0;
 #pragma unroll
         for (int w = 0; w < C::Wy; ++w) f ^= y[w];
+        // low five bits (and for two words the sixth, the parity of word 1),
+        // gathered from parity-count fields as in the one-word case
+        constexpr int MG = C::Wy == 2 ? 6 : 5;
+        using SG = SynGather<MG>;
+        uint32_t pf = __popc(f & bmask(0));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) s |= (__popc(f & bmask(i)) & 1u) << i;
+        for (int i = 1; i < 5; ++i) pf = fma_lo(__popc(f & bmask(i)), 1u << (SG::F * i), pf);
+        if constexpr (MG == 6) pf = fma_lo(__popc(y[1]), 1u << (SG::F * 5), pf);
+        s = ((pf & SG::lsbs()) * SG::mult()) >> (32 - MG);
 #pragma unroll
-        for (int t = 0; (1 << t) < C::Wy; ++t) {
+        for (int t = MG - 5; (1 << t) < C::Wy; ++t) {
             uint32_t g = 0;
 #pragma unroll
             for (int w = 0; w < C::Wy; ++w)
@@ -283,65 +310,88 @@ __device__ __forceinline__ uint32_t part_syndrome(const uint32_t (&y)[Code<N_>::
 // decides the correction (P = 1: flip position s; P = 0: flip nothing, and
 // s != 0 is a detected double error, counted in `det`); the syndrome value is
 // s | P << m.
-template <int N_, int G, int R, bool XH = false, class OP, class SP>
-__device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &sp, uint32_t &det)
+template <int N_, int G, int R, bool XH = false, bool LUT = false, class OP, class SP>
+__device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &sp, uint32_t &det,
+                                            const uint16_t *lut = nullptr)
 {
     using C = Code<N_>;
+    if constexpr (LUT) {
+        // one lookup per codeword: its n bits index data | s << k.  All G
+        // lookups are issued before any result is packed, so their shared
+        // memory latencies overlap.
+        static_assert(N_ <= 15 && !XH, "decode tables exist for n = 7 and 15");
+        uint32_t e[G];
 #pragma unroll
-    for (int c = 0; c < G; ++c) {
-        uint32_t y[C::Wy];
+        for (int c = 0; c < G; ++c) {
+            const int start = c * N_;  // a constant once the loop is unrolled
+            const int a = start >> 5, sh = start & 31;
+            uint32_t v;
+            if (sh == 0)
+                v = r[a];
+            else if (a + 1 < R)
+                v = __funnelshift_r(r[a], r[a + 1], sh);
+            else
+                v = r[a] >> sh;
+            e[c] = lut[v & ((1u << N_) - 1u)];
+        }
 #pragma unroll
-        for (int w = 0; w < C::Wy; ++w) y[w] = XH ? part_y_xh<N_, R>(r, c, w) : part_y<N_, R>(r, c, w);
-        if constexpr (C::Wy == 1) {
-            // checksum: parities of y & I_i, summed into fields, gathered into
-            // the top m bits of st
-            using SG = SynGather<C::m>;
-            uint32_t pf = __popc(y[0] & qmask(N_, 0));
+        for (int c = 0; c < G; ++c) {
+            op.append(e[c] & ((1u << C::k) - 1u), C::k);
+            sp.put(c, e[c] >> C::k);
+        }
+    } else {
 #pragma unroll
-            for (int i = 1; i < C::m; ++i) pf = fma_lo(__popc(y[0] & qmask(N_, i)), 1u << (SG::F * i), pf);
-            const uint32_t st = (pf & SG::lsbs()) * SG::mult();
-            const uint32_t s = fma_hi(st, 1u << C::m, 0u);  // st >> (32 - m)
-            // correction: flip position s (s = 0 flips bit 0, which is no data position)
-            if constexpr (XH) {
-                const uint32_t P = __popc(y[0]) & 1u;
-                y[0] ^= P << s;
-                det += (P == 0u && s != 0u) ? 1u : 0u;
-                sp.put(c, s | (P << C::m));
+        for (int c = 0; c < G; ++c) {
+            uint32_t y[C::Wy];
+#pragma unroll
+            for (int w = 0; w < C::Wy; ++w) y[w] = XH ? part_y_xh<N_, R>(r, c, w) : part_y<N_, R>(r, c, w);
+            if constexpr (C::Wy == 1) {
+                // checksum: parities of y & I_i, summed into fields, gathered into
+                // the top m bits of st
+                using SG = SynGather<C::m>;
+                uint32_t pf = __popc(y[0] & qmask(N_, 0));
+#pragma unroll
+                for (int i = 1; i < C::m; ++i) pf = fma_lo(__popc(y[0] & qmask(N_, i)), 1u << (SG::F * i), pf);
+                const uint32_t st = (pf & SG::lsbs()) * SG::mult();
+                const uint32_t s = st >> (32 - C::m);
+                // correction: flip position s (s = 0 flips bit 0, which is no data position)
+                if constexpr (XH) {
+                    const uint32_t P = __popc(y[0]) & 1u;
+                    y[0] ^= P << s;
+                    det += (P == 0u && s != 0u) ? 1u : 0u;
+                    sp.put(c, s | (P << C::m));
+                } else {
+                    y[0] ^= 1u << s;
+                }
+                // redundancy removal
+                uint32_t d = compress_runs<C::m>(y[0]);
+                if constexpr (C::m < 5) d &= (1u << C::k) - 1u;  // the word also holds the next codeword
+                op.append(d, C::k);
+                if constexpr (!XH) sp.put(c, s);
             } else {
-                y[0] ^= 1u << s;
+                const uint32_t s = part_syndrome<N_>(y);
+                uint32_t sf = s;  // the position to flip; past every word when nothing is flipped
+                if constexpr (XH) {
+                    uint32_t f = 0;
+#pragma unroll
+                    for (int w = 0; w < C::Wy; ++w) f ^= y[w];
+                    const uint32_t P = __popc(f) & 1u;
+                    sf = P ? s : 0xFFFFFFFFu;
+                    det += (P == 0u && s != 0u) ? 1u : 0u;
+                    sp.put(c, s | (P << C::m));
+                }
+#pragma unroll
+                for (int w = 0; w < C::Wy; ++w) y[w] ^= shl_clamp(1u, sf - 32u * (uint32_t)w);
+                op.append(compress_runs<5>(y[0]), 26);
+#pragma unroll
+                for (int w = 1; w < C::Wy; ++w) {
+                    if ((w & (w - 1)) == 0)
+                        op.append(y[w] >> 1, 31);  // position 32w is a checksum position
+                    else
+                        op.append(y[w], 32);
+                }
+                if constexpr (!XH) sp.put(c, s);
             }
-            // redundancy removal: run j moves down by j + 2 bits (high product)
-            uint32_t d = 0;
-#pragma unroll
-            for (int j = 1; j < C::m; ++j) d = fma_hi(y[0] & (run_mask(j) << (j + 2)), 1u << (30 - j), d);
-            op.append(d, C::k);
-            if constexpr (!XH) sp.put(c, s);
-        } else {
-            const uint32_t s = part_syndrome<N_>(y);
-            uint32_t sf = s;  // the position to flip; past every word when nothing is flipped
-            if constexpr (XH) {
-                uint32_t f = 0;
-#pragma unroll
-                for (int w = 0; w < C::Wy; ++w) f ^= y[w];
-                const uint32_t P = __popc(f) & 1u;
-                sf = P ? s : 0xFFFFFFFFu;
-                det += (P == 0u && s != 0u) ? 1u : 0u;
-                sp.put(c, s | (P << C::m));
-            }
-#pragma unroll
-            for (int w = 0; w < C::Wy; ++w) y[w] ^= shl_clamp(1u, sf - 32u * (uint32_t)w);
-            uint32_t d0 = 0;
-#pragma unroll
-            for (int j = 1; j < 5; ++j) d0 |= (y[0] >> (j + 2)) & run_mask(j);
-            op.append(d0, 26);
-#pragma unroll
-            for (int w = 1; w < C::Wy; ++w) {
-                if ((w & (w - 1)) == 0)
-                    op.append(y[w] >> 1, 31);  // position 32w is a checksum position
-                else
-                    op.append(y[w], 32);
-            }
-            if constexpr (!XH) sp.put(c, s);
         }
     }
     op.finish();

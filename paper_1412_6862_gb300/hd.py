@@ -37,7 +37,8 @@ class VariantInfo(ctypes.Structure):
     """Mirror of hd_variant_info."""
     _fields_ = [("index", _u32), ("n", _u32), ("syn_type", _u32), ("codewords_per_thread", _u32),
                 ("threads", _u32), ("stages", _u32), ("inplace", _u32), ("smem_bytes", _u32),
-                ("chunk_codewords", _u64), ("blocks_per_sm", _c.c_int32), ("measured_us", _c.c_float)]
+                ("chunk_codewords", _u64), ("blocks_per_sm", _c.c_int32), ("measured_us", _c.c_float),
+                ("table_lookup", _u32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
