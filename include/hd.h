@@ -296,6 +296,10 @@ typedef struct {
     uint64_t codewords;     /* over all packets */
     uint64_t in_bytes, out_bytes, syn_bytes;
     float measured_us;      /* hd_plan_autotune's time for the best configuration, -1 if not tuned */
+    uint32_t table_lookup;  /* decode tables the configuration uses: bit 0 n = 7 (256 B per CTA),
+                               bit 1 n = 15 (64 KB per CTA); each is filled on the launching stream on
+                               first use per device (that call synchronises the stream; a launch whose
+                               stream is capturing before then decodes without the table) */
 } hd_plan_info;
 
 /* Validate the table (HD_ERR_INVALID_N / NULL / ALIGN / SIZE for the first bad

@@ -51,59 +51,94 @@ __host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 255 ? 8 : (n
 __host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 15 ? 4 : (n <= 31 ? 2 : 1); }
 
 constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest tile input (n=255: 8160 B; n=31: 7936 B) + spare
-constexpr uint32_t kBatchSynBytes = 4 * 32 * 32 * 2;  // largest tile syndromes (4 chunks of 1024, u16)
+// Full tiles write their syndromes straight to global memory (each lane's run
+// of G syndromes is contiguous); only a ragged tail, at most one chunk, stages
+// them here before the copy that keeps within the packet.
+constexpr uint32_t kBatchSynBytes = 32 * 32 * 2;  // one chunk of at most 1024 codewords, u16
 
-template <int WARPS, int S>
+template <int WARPS, int S, bool T15>
 struct BatchCfg {
     static constexpr uint32_t off_bar = 0;
     static constexpr uint32_t off_claim = 64;  // per stage: the claimed tile index and its descriptor
     static constexpr uint32_t off_desc = 128;
     static constexpr uint32_t off_stage = off_desc + 8 * 64;
     static constexpr uint32_t off_syn = off_stage + S * kBatchStageBytes;
-    // one syndrome buffer: every store has read its sources before the next tile starts
     static constexpr uint32_t warp_bytes = (off_syn + kBatchSynBytes + 127) / 128 * 128;
-    static constexpr uint32_t smem = WARPS * warp_bytes;
-    static_assert(S >= 1 && S <= 8, "stages");
+    // behind the warps' areas: the n = 7 decode table, (T15) the n = 15 one,
+    // and the mbarrier of the n = 15 table's bulk copies
+    static constexpr uint32_t off_lut7 = WARPS * warp_bytes;
+    static constexpr uint32_t off_lut15 = off_lut7 + (2u << 7);
+    static constexpr uint32_t lut15_bytes = T15 ? (2u << 15) : 0u;
+    static constexpr uint32_t off_lut_bar = off_lut15 + lut15_bytes;
+    static constexpr uint32_t smem = off_lut_bar + 16;
+    static_assert(S >= 2 && S <= 8, "refills lag one iteration: at least two stages");
     static_assert(kWarpSlotWords * 4 * 2 <= kBatchStageBytes, "generic slots fit a stage");
     static_assert(smem <= 232448, "shared memory per CTA");
 };
 
 // Decode the `chunks` whole chunks of a full tile held in `stage`, in place:
 // chunk c's output goes to stage + c*out_words, which never overlaps a later
-// chunk's input because k < n.
-template <int N_, int SYN>
-__device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sbuf, int lane, uint32_t chunks)
+// chunk's input because k < n.  Chunk c's syndromes go to sdst + c * (bytes of
+// one chunk's syndromes): global memory for a full tile, the warp's staging
+// buffer for a tail.
+template <int N_, int SYN, bool LUT>
+__device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sdst, int lane, uint32_t chunks,
+                                                const uint16_t *lut)
 {
     using Q = ChunkGeom<N_, SYN, batch_G(N_)>;
     uint32_t e = 0, unused = 0;
     for (uint32_t c = 0; c < chunks; ++c)
-        e += decode_warp_chunk<N_, SYN, batch_G(N_)>(stage + c * Q::in_words,
-                                                      const_cast<uint32_t *>(stage) + c * Q::out_words,
-                                                      sbuf + c * Q::syn_bytes, lane, unused);
+        e += decode_warp_chunk<N_, SYN, batch_G(N_), false, LUT>(stage + c * Q::in_words,
+                                                                  const_cast<uint32_t *>(stage) + c * Q::out_words,
+                                                                  sdst + c * Q::syn_bytes, lane, unused, lut);
     return e;
 }
 
-template <int N_>
-__device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sbuf, int lane,
-                                                    uint32_t chunks)
+// LUT: decode with the table `lut` in shared memory (n = 7 and 15 only).
+template <int N_, bool LUT = false>
+__device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sdst, int lane,
+                                                    uint32_t chunks, const uint16_t *lut = nullptr)
 {
     switch (syn_type) {
-        case 1: return batch_chunk<N_, 1>(stage, sbuf, lane, chunks);
-        case 2: return batch_chunk<N_, 2>(stage, sbuf, lane, chunks);
-        default: return batch_chunk<N_, 0>(stage, sbuf, lane, chunks);
+        case 1: return batch_chunk<N_, 1, LUT>(stage, sdst, lane, chunks, lut);
+        case 2: return batch_chunk<N_, 2, LUT>(stage, sdst, lane, chunks, lut);
+        default: return batch_chunk<N_, 0, LUT>(stage, sdst, lane, chunks, lut);
     }
 }
 
 __device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return 32u * (uint32_t)batch_G(n); }
 
-template <int WARPS, int S>
+// lut7 (or nullptr: arithmetic decode) and, with T15, lut15 (required) are
+// the global decode tables of n = 7 and 15; the kernel copies them into shared
+// memory once per CTA.
+template <int WARPS, int S, bool T15>
 __global__ void __launch_bounds__(WARPS * 32)
     k_decode_batch(const DevTile *__restrict__ tiles, uint32_t num_tiles, uint32_t *__restrict__ counter,
-                   unsigned long long *__restrict__ err_counts, uint32_t *__restrict__ status)
+                   unsigned long long *__restrict__ err_counts, uint32_t *__restrict__ status,
+                   const uint16_t *__restrict__ lut7, const uint16_t *__restrict__ lut15)
 {
-    using Cfg = BatchCfg<WARPS, S>;
+    using Cfg = BatchCfg<WARPS, S, T15>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *lut_bar = reinterpret_cast<uint64_t *>(smem + Cfg::off_lut_bar);
+    if constexpr (T15) {
+        // the n = 15 table: bulk copies on the CTA's table barrier, in flight
+        // while the warps claim and load their first tiles
+        if (threadIdx.x == 0) {
+            mbar_init(lut_bar, 1);
+            fence_mbar_init();
+            mbar_arrive_expect_tx(lut_bar, Cfg::lut15_bytes);
+#pragma unroll
+            for (uint32_t o = 0; o < Cfg::lut15_bytes; o += 16384u)
+                bulk_g2s(smem + Cfg::off_lut15 + o, reinterpret_cast<const uint8_t *>(lut15) + o, 16384u, lut_bar);
+        }
+    }
+    if (lut7 != nullptr && threadIdx.x < 16)  // 256 bytes
+        reinterpret_cast<uint4 *>(smem + Cfg::off_lut7)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint4 *>(lut7) + threadIdx.x);
+    __syncthreads();  // the n = 7 table is in place and the table barrier initialised
+    const uint16_t *s_lut7 = reinterpret_cast<const uint16_t *>(smem + Cfg::off_lut7);
+    const uint16_t *s_lut15 = reinterpret_cast<const uint16_t *>(smem + Cfg::off_lut15);
     uint8_t *wbase = smem + warp * Cfg::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
     volatile uint32_t *claim = reinterpret_cast<volatile uint32_t *>(wbase + Cfg::off_claim);
@@ -144,7 +179,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 
     uint32_t it = 0;
     bool aborted = false;
-    for (;; ++it) {
+    if constexpr (T15) aborted = __any_sync(0xFFFFFFFFu, !mbar_wait_bounded(lut_bar, 0));
+    for (; !aborted; ++it) {
         const int s = (int)(it % S);
         const bool ok = mbar_wait_bounded(&bar[s], (it / S) & 1u);
         if (__any_sync(0xFFFFFFFFu, !ok)) {
@@ -153,10 +189,11 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         const uint32_t t = claim[s];
         if (t >= num_tiles) break;  // claims only grow: every later stage is past the end too
-        // every iteration refills its stage at its end: fetch the descriptor of
-        // the tile claimed last iteration and claim the next one
+        // from the second iteration on, every iteration refills the previous
+        // iteration's stage at its end: fetch the descriptor of the tile claimed
+        // last iteration and claim the next one
         uint32_t later_t = 0;
-        if (lane == 0) {
+        if (lane == 0 && it > 0) {
             if (next_t < num_tiles) next_d = tiles[next_t];  // used at the end of this iteration
             later_t = atomicAdd(counter, 1u);                // used at the end of the next one
         }
@@ -173,6 +210,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         const uint32_t chunks = full ? (tl.count & ~kFullTile) / chunk_codewords(p.n) : 0u;
         uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * kBatchStageBytes);
         uint8_t *sbuf = s_syn;
+        uint8_t *sdst = (full && p.syn_type != 0) ? p.syn + tl.c0 * (p.syn_type == 2 ? 2u : 1u) : sbuf;
         unsigned long long errs = 0;
         if (full || p.n != 3) {
             const uint32_t cwords = chunk_codewords(p.n);
@@ -195,12 +233,20 @@ __global__ void __launch_bounds__(WARPS * 32)
             uint32_t e = 0;
             const uint32_t nch = full ? chunks : 1u;
             switch (p.n) {
-                case 7: e = batch_chunk_syn<7>(p.syn_type, stage, sbuf, lane, nch); break;
-                case 15: e = batch_chunk_syn<15>(p.syn_type, stage, sbuf, lane, nch); break;
-                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sbuf, lane, nch); break;
-                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sbuf, lane, nch); break;
-                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sbuf, lane, nch); break;
-                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sbuf, lane, nch); break;
+                case 7:
+                    e = lut7 != nullptr ? batch_chunk_syn<7, true>(p.syn_type, stage, sdst, lane, nch, s_lut7)
+                                        : batch_chunk_syn<7>(p.syn_type, stage, sdst, lane, nch);
+                    break;
+                case 15:
+                    if constexpr (T15)
+                        e = batch_chunk_syn<15, true>(p.syn_type, stage, sdst, lane, nch, s_lut15);
+                    else
+                        e = batch_chunk_syn<15>(p.syn_type, stage, sdst, lane, nch);
+                    break;
+                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sdst, lane, nch); break;
+                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sdst, lane, nch); break;
+                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sdst, lane, nch); break;
+                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sdst, lane, nch); break;
                 default: break;  // the plan never makes chunk tiles of other lengths
             }
 #pragma unroll
@@ -228,21 +274,20 @@ __global__ void __launch_bounds__(WARPS * 32)
             __syncwarp();
         }
         if (lane == 0) {
+            // the previous iteration's stage held that tile's output; its store
+            // has had this whole decode to read it: refill the stage with the
+            // tile claimed last iteration (so the lookahead is S - 1 tiles)
+            if (it > 0) {
+                bulk_wait_read<0>();
+                issue((int)((it - 1) % S), next_t, next_d);
+                next_t = later_t;
+            }
             if (full) {
                 const uint32_t cw = tl.count & ~kFullTile;
                 const uint32_t k = p.n - p.m;
                 bulk_s2g(p.out + tl.c0 * k / 32u, stage, cw * k / 8u);
-                if (p.syn_type != 0) {
-                    const uint32_t sb = p.syn_type == 2 ? 2u : 1u;
-                    bulk_s2g(p.syn + tl.c0 * sb, sbuf, cw * sb);
-                }
                 bulk_commit();
             }
-            // the stage holds this tile's output: once the store has read it,
-            // refill the stage with the tile claimed last iteration
-            bulk_wait_read<0>();
-            issue(s, next_t, next_d);
-            next_t = later_t;
             if (err_counts != nullptr && errs != 0) atomicAdd(&err_counts[tl.packet], errs);
         }
         __syncwarp();
@@ -250,7 +295,11 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (lane == 0) {
         if (aborted) {
             atomicOr(status, (uint32_t)HD_ERR_TIMEOUT);
-            for (uint32_t j = it; j < it + S; ++j) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+            // loads still in flight: the S of the prologue before the first
+            // iteration, afterwards S - 1 (refills lag one iteration)
+            const uint32_t pending = it > 0 ? S - 1 : S;
+            for (uint32_t j = it; j < it + pending; ++j) (void)mbar_wait_bounded(&bar[j % S], (j / S) & 1u);
+            if constexpr (T15) (void)mbar_wait_bounded(lut_bar, 0);
         }
         bulk_wait_all<0>();
     }
@@ -261,35 +310,42 @@ __global__ void __launch_bounds__(WARPS * 32)
 // ---------------------------------------------------------------------------
 struct BatchVariant {
     int warps, stages;
+    bool t15;  // holds the n = 15 decode table (needs it at launch)
     uint32_t smem;
     const void *kernel;
     void (*launch)(int grid, uint32_t smem, cudaStream_t st, const DevTile *, uint32_t, uint32_t *,
-                   unsigned long long *, uint32_t *);
+                   unsigned long long *, uint32_t *, const uint16_t *, const uint16_t *);
 };
 
-template <int W, int S>
+template <int W, int S, bool T15>
 void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevTile *tiles, uint32_t num_tiles,
-                         uint32_t *counter, unsigned long long *err, uint32_t *status)
+                         uint32_t *counter, unsigned long long *err, uint32_t *status, const uint16_t *lut7,
+                         const uint16_t *lut15)
 {
-    k_decode_batch<W, S><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status);
+    k_decode_batch<W, S, T15><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status, lut7, lut15);
 }
 
-template <int W, int S>
+template <int W, int S, bool T15 = false>
 BatchVariant make_batch_variant()
 {
     BatchVariant v;
     v.warps = W;
     v.stages = S;
-    v.smem = BatchCfg<W, S>::smem;
-    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S>);
-    v.launch = &launch_batch_kernel<W, S>;
+    v.t15 = T15;
+    v.smem = BatchCfg<W, S, T15>::smem;
+    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S, T15>);
+    v.launch = &launch_batch_kernel<W, S, T15>;
     return v;
 }
 
 static const std::vector<BatchVariant> &batch_variants()
 {
-    static const std::vector<BatchVariant> v = {make_batch_variant<2, 2>(), make_batch_variant<1, 3>(),
-                                                make_batch_variant<2, 3>(), make_batch_variant<1, 4>()};
+    // index 0 is the built-in choice (and the serving and allocation-free
+    // paths' configuration); it holds no n = 15 table
+    static const std::vector<BatchVariant> v = {
+        make_batch_variant<1, 2>(),       make_batch_variant<1, 3>(),       make_batch_variant<2, 2>(),
+        make_batch_variant<2, 3>(),       make_batch_variant<4, 2>(),       make_batch_variant<8, 2, true>(),
+        make_batch_variant<6, 2, true>(), make_batch_variant<6, 3, true>(), make_batch_variant<4, 3, true>()};
     return v;
 }
 
@@ -399,23 +455,32 @@ int batch_grid(const BatchVariant &v, uint32_t num_tiles)
 }
 
 // Resolve everything that touches device state before a (possibly captured)
-// enqueue: kernel attributes, occupancy and the status word address.
+// enqueue: kernel attributes, occupancy, the status word address and the
+// decode tables (filled on `st` on first use; `st` must not be capturing for
+// that, else the n = 7 tiles decode arithmetically and a configuration that
+// holds the n = 15 table gives way to the built-in one).
 struct LaunchGeom {
+    int variant;
     int grid;
     uint32_t *status;
+    const uint16_t *lut7, *lut15;
 };
 
-cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g)
+cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
 {
     g->status = status_ptr();
     if (g->status == nullptr) return cudaErrorInvalidSymbol;
-    g->grid = batch_grid(batch_variants()[p->variant], p->num_tiles);
+    g->variant = p->variant;
+    g->lut7 = lut_ptr(7, st);
+    g->lut15 = batch_variants()[g->variant].t15 ? lut_ptr(15, st) : nullptr;
+    if (batch_variants()[g->variant].t15 && g->lut15 == nullptr) g->variant = 0;
+    g->grid = batch_grid(batch_variants()[g->variant], p->num_tiles);
     return g->grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
 cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *err_counts, cudaStream_t st)
 {
-    const BatchVariant &v = batch_variants()[p->variant];
+    const BatchVariant &v = batch_variants()[g.variant];
     const int grid = g.grid;
     uint32_t *status = g.status;
     cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t), st);
@@ -425,7 +490,7 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
         if (e != cudaSuccess) return e;
     }
     if (p->num_tiles == 0) return cudaSuccess;
-    v.launch(grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status);
+    v.launch(grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15);
     return cudaGetLastError();
 }
 
@@ -461,7 +526,7 @@ cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32
     p.d_tiles = const_cast<DevTile *>(d_tiles);
     p.d_counter = d_counter;
     LaunchGeom geom;
-    cudaError_t e = prepare_plan(&p, &geom);
+    cudaError_t e = prepare_plan(&p, &geom, st);
     if (e == cudaSuccess) e = enqueue_plan(&p, geom, d_err, st);
     if (e == cudaSuccess && num_tiles) count_launch();
     return e;
@@ -512,7 +577,7 @@ hd_status hd_plan_launch(hd_plan *p, unsigned long long *err_counts, void *cuda_
     if (!p->graph_ok || p->graph_err != err_counts) {
         drop_graph(p);
         LaunchGeom geom;
-        if (prepare_plan(p, &geom) != cudaSuccess) return HD_ERR_CUDA;
+        if (prepare_plan(p, &geom, st) != cudaSuccess) return HD_ERR_CUDA;
         if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HD_ERR_CUDA;
         const cudaError_t e = enqueue_plan(p, geom, err_counts, p->capture);
         cudaGraph_t g = nullptr;
@@ -548,7 +613,7 @@ hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan
     for (size_t i = 0; i < batch_variants().size(); ++i) {
         p->variant = (int)i;
         LaunchGeom geom;
-        if (prepare_plan(p, &geom) != cudaSuccess) continue;
+        if (prepare_plan(p, &geom, st) != cudaSuccess || geom.variant != (int)i) continue;
         if (enqueue_plan(p, geom, nullptr, st) != cudaSuccess) {
             rc = HD_ERR_CUDA;
             break;
@@ -596,6 +661,7 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
     info->variant = (uint32_t)p->variant;
     info->num_variants = (uint32_t)batch_variants().size();
     info->measured_us = p->tuned_us;
+    info->table_lookup = 1u | (v.t15 ? 2u : 0u);
     return HD_OK;
 }
 
@@ -640,7 +706,7 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
         return HD_ERR_CUDA;
     }
     LaunchGeom geom;
-    cudaError_t e = prepare_plan(&p, &geom);
+    cudaError_t e = prepare_plan(&p, &geom, st);
     if (e == cudaSuccess) e = enqueue_plan(&p, geom, err_counts, st);
     if (p.num_tiles && e == cudaSuccess) count_launch();
     cudaFreeAsync(p.dmem, st);
@@ -774,8 +840,9 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
     const BatchVariant &v = batch_variants()[0];
     const int grid = batch_grid(v, t);
     if (grid <= 0) return HD_ERR_CUDA;
+    // no decode tables: this path never fills or synchronises anything
     v.launch(grid, v.smem, st, reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
-             g_noalloc_status[dev]);
+             g_noalloc_status[dev], nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
     count_launch();
     return HD_OK;

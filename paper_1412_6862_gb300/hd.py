@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("num_packets", _u32), ("num_tiles", _u32), ("full_tiles", _u32), ("warps_per_cta", _u32),
                 ("stages", _u32), ("smem_bytes", _u32), ("variant", _u32), ("num_variants", _u32),
                 ("codewords", _u64), ("in_bytes", _u64), ("out_bytes", _u64), ("syn_bytes", _u64),
-                ("measured_us", _c.c_float)]
+                ("measured_us", _c.c_float), ("table_lookup", _u32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
