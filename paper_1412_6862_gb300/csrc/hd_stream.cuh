@@ -123,9 +123,11 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
 }
 
 // Every warp is an independent pipeline: it owns S input stages with one
-// mbarrier each, (unless INPLACE) two output staging buffers, and two syndrome
-// buffers.  Lane 0 issues the warp's bulk loads and stores; warps never wait
-// for one another, so one warp's memory wait overlaps the others' arithmetic.
+// mbarrier each and (unless INPLACE) two output staging buffers.  Lane 0
+// issues the warp's bulk loads and data stores; the syndromes go from the
+// lanes' registers straight to global memory (each lane's run of G syndromes
+// is contiguous, stored in 16-byte vectors).  Warps never wait for one
+// another, so one warp's memory wait overlaps the others' arithmetic.
 template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     using Q = ChunkGeom<N_, SYN, G, XH>;
@@ -136,8 +138,7 @@ struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     static constexpr uint32_t off_bar = 0;
     static constexpr uint32_t off_in = 64;
     static constexpr uint32_t off_out = off_in + S * stage_bytes;
-    static constexpr uint32_t off_syn = off_out + (INPLACE ? 0 : 2 * out_buf_bytes);
-    static constexpr uint32_t warp_bytes = (off_syn + 2 * Q::syn_bytes + 127) / 128 * 128;
+    static constexpr uint32_t warp_bytes = (off_out + (INPLACE ? 0 : 2 * out_buf_bytes) + 127) / 128 * 128;
     static constexpr uint32_t lut_bytes = LUT ? (2u << N_) : 0u;  // u16 per codeword value
     static constexpr uint32_t off_lut = WARPS * warp_bytes;         // the table, then its mbarrier
     static constexpr uint32_t smem = off_lut + (LUT ? lut_bytes + 16u : 0u);
@@ -197,7 +198,6 @@ __global__ void __launch_bounds__(T)
     uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + Cfg::off_bar);
     uint8_t *s_in = wbase + Cfg::off_in;
     uint8_t *s_out = wbase + Cfg::off_out;
-    uint8_t *s_syn = wbase + Cfg::off_syn;
     const uint64_t gw = (uint64_t)blockIdx.x * Cfg::WARPS + warp;  // global warp index
     const uint64_t tw = (uint64_t)gridDim.x * Cfg::WARPS;          // warps in the grid
 
@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(T)
         const uint32_t *stage = reinterpret_cast<const uint32_t *>(s_in + s * Cfg::stage_bytes);
         uint32_t *obase = INPLACE ? reinterpret_cast<uint32_t *>(s_in + s * Cfg::stage_bytes)
                                   : reinterpret_cast<uint32_t *>(s_out + ob * Cfg::out_buf_bytes);
-        errs += decode_warp_chunk<N_, SYN, G, XH, LUT>(stage, obase, s_syn + ob * Cfg::syn_bytes, lane, dets, s_lut);
+        // syndromes go straight to global memory: each lane's run of G is contiguous
+        uint8_t *sdst = SYN != 0 ? syn + c * (uint64_t)Cfg::syn_bytes : s_in;
+        errs += decode_warp_chunk<N_, SYN, G, XH, LUT>(stage, obase, sdst, lane, dets, s_lut);
         fence_proxy_async_smem();
         __syncwarp();
         if constexpr (Cfg::PADDED) {
@@ -271,8 +273,6 @@ __global__ void __launch_bounds__(T)
             }
             if (lane == 0) {
                 bulk_s2g(out + c * (uint64_t)Cfg::out_words, obase, Cfg::out_bytes);
-                if constexpr (SYN != 0)
-                    bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
                 bulk_commit();
             }
             if constexpr (!INPLACE) {
@@ -295,8 +295,6 @@ __global__ void __launch_bounds__(T)
                 }
             }
             bulk_s2g(out + c * (uint64_t)Cfg::out_words, obase, Cfg::out_bytes);
-            if constexpr (SYN != 0)
-                bulk_s2g(syn + c * (uint64_t)Cfg::syn_bytes, s_syn + ob * Cfg::syn_bytes, Cfg::syn_bytes);
             bulk_commit();
             if constexpr (!INPLACE) {
                 // the stage was consumed by this iteration: prefetch the chunk S iterations ahead
@@ -386,8 +384,7 @@ StreamVariant make_variant()
     return v;
 }
 
-// Every syndrome type of one configuration whose shared memory fits a CTA
-// (the u16 syndrome buffers are twice the u8 ones).
+// Every syndrome type of one configuration whose shared memory fits a CTA.
 template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH, bool LUT>
 void add_variant_if_fits(std::vector<StreamVariant> &out)
 {

@@ -33,12 +33,18 @@ void register_stream_a(std::vector<StreamVariant> &v)
     add_variants<15, 640, 3, 32, 1, false, true>(v);
     add_variants<15, 512, 2, 32, 0, false, true>(v);  // separate output buffers: lookahead S
     add_variants<15, 576, 2, 32, 0, false, true>(v);
+    add_variants<15, 640, 2, 32, 0, false, true>(v);
+    add_variants<15, 576, 3, 32, 0, false, true>(v);
+    add_variants<15, 1024, 2, 32, 1, false, true>(v);
     // n = 31
     add_variants<31, 128, 4, 32, 0>(v);
     add_variants<31, 128, 4, 32, 1>(v);
     add_variants<31, 128, 3, 32, 1>(v);
     add_variants<31, 256, 2, 32, 1>(v);
     add_variants<31, 256, 3, 16, 1>(v);
+    add_variants<31, 96, 3, 32, 1>(v);
+    add_variants<31, 96, 4, 32, 1>(v);
+    add_variants<31, 64, 3, 32, 1>(v);
 }
 
 }  // namespace hd
