@@ -254,9 +254,13 @@ hd_status hd_variant_select(uint32_t n, hd_syn_type syn_type, int32_t ordinal);
 hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *info);
 
 /* Time every configuration of (n, syn_type) on `num_codewords` codewords of
- * scratch data (allocated and freed here; `reps` timed launches each, 0 = 5)
- * on `cuda_stream`, keep the fastest for this device and report it in
- * *chosen (may be NULL).  Synchronises the stream. */
+ * random scratch data (allocated and freed here: enough buffer sets, at most
+ * 8, that one pass over them streams twice the L2 size) on `cuda_stream`;
+ * `reps` rounds (0 = 5) launch every configuration once per round over all
+ * sets, and a configuration's time is its median round.  The fastest is kept
+ * for this device, except that the built-in choice stays unless it is more
+ * than 2 % slower; the choice is reported in *chosen (may be NULL).
+ * Synchronises the stream. */
 hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,
                       hd_variant_info *chosen);
 
