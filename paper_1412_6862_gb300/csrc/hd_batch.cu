@@ -5,14 +5,15 @@
 // cut into full warp chunks of 32*G codewords (G = 32 for n <= 63, 16 for
 // n = 127, 8 for n = 255, so a chunk's input is at most 8 KB) and, when its
 // length is not a multiple of that, one ragged tail tile.  Warps of a
-// persistent kernel claim tiles from an atomic counter in table order (full
-// tiles grouped by n, then the tails), prefetch S claimed tiles ahead into
-// their own shared-memory stages with 1-D bulk copies, decode full tiles with
-// the same per-warp chunk decoder as the streaming kernel, decode tails with
-// the chunk decoder too (copied in, zero-padded to a chunk, copied back out;
-// n = 3 tails use the generic warp-tile decoder), and add each tile's
-// nonzero-syndrome count to its packet's error counter.  Dynamic claiming of
-// bounded tiles balances packets whose lengths span six orders of magnitude.
+// persistent kernel claim tiles from an atomic counter in table order (tiles
+// grouped by n, each code's tails spread among its full tiles), prefetch
+// claimed tiles into their own shared-memory stages with 1-D bulk copies,
+// decode full tiles with the same per-warp chunk decoder as the streaming
+// kernel, decode tails with the chunk decoder too (copied in, zero-padded to a
+// chunk, copied back out; n = 3 tails use the generic warp-tile decoder), and
+// add each tile's nonzero-syndrome count to its packet's error counter.
+// Dynamic claiming of bounded tiles balances packets whose lengths span six
+// orders of magnitude.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -49,6 +50,70 @@ __host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 255 ? 8 : (n
 // codewords) so that every tile moves several KB and the per-tile overhead
 // and load latency are amortised.
 __host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 15 ? 4 : (n <= 31 ? 2 : 1); }
+
+// One packet as the tile builders see it.
+struct PacketView {
+    const uint32_t *in;
+    uint32_t *out;
+    uint8_t *syn;
+    uint64_t num_cw;
+    uint32_t n, m, syn_type;
+};
+
+// Emit the tiles of every packet of code length n, without allocating: full
+// tiles in packet order, with the packets' ragged tails spread evenly among
+// them (after each full tile, tails until their share matches), so that the
+// latency-bound tails overlap the streaming of full tiles instead of running
+// as a phase of their own.  view(i) describes packet i; emit(tile) takes a tile.
+template <class View, class Emit>
+void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit)
+{
+    const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+    const uint64_t per = (uint64_t)batch_chunks(n);
+    auto nfull_of = [&](const PacketView &p) { return n == 3 ? 0 : p.num_cw / chunk; };  // n = 3: all tail
+    uint64_t nf = 0, nt = 0;  // full tiles and tail tiles of this n
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const PacketView p = view(i);
+        if (p.n != n) continue;
+        const uint64_t f = nfull_of(p);
+        nf += (f + per - 1) / per;
+        nt += (p.num_cw - f * chunk + kTailTile - 1) / kTailTile;
+    }
+    uint32_t ti = 0;  // tail cursor: packet and next codeword
+    uint64_t tc = 0;
+    auto next_tail = [&]() -> bool {
+        for (; ti < num_packets; ++ti, tc = 0) {
+            const PacketView p = view(ti);
+            if (p.n != n) continue;
+            tc = std::max(tc, nfull_of(p) * chunk);
+            if (tc < p.num_cw) {
+                // a chunk-decoded tail prefetches the whole 16-byte groups of its
+                // input with the stage's bulk copy (it starts on a chunk boundary,
+                // so 16-byte aligned); the last words are loaded when it is decoded
+                const uint32_t cnt = (uint32_t)std::min<uint64_t>(kTailTile, p.num_cw - tc);
+                const uint32_t bulk = n == 3 ? 0u : (uint32_t)(((uint64_t)cnt * n + 31) / 32 * 4) & ~15u;
+                emit(make_tile(p.in, p.out, p.syn, p.num_cw, n, p.m, p.syn_type, ti, tc, cnt, bulk));
+                tc += kTailTile;
+                return true;
+            }
+        }
+        return false;
+    };
+    uint64_t done_full = 0, done_tail = 0;
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const PacketView p = view(i);
+        if (p.n != n) continue;
+        const uint64_t f = nfull_of(p);
+        for (uint64_t j = 0; j < f; j += per) {
+            const uint64_t c = std::min(per, f - j);
+            emit(make_tile(p.in, p.out, p.syn, p.num_cw, n, p.m, p.syn_type, i, j * chunk,
+                           (uint32_t)(c * chunk) | kFullTile, (uint32_t)(c * chunk * n / 8)));
+            ++done_full;
+            while (done_tail * nf < done_full * nt && next_tail()) ++done_tail;
+        }
+    }
+    while (next_tail()) ++done_tail;
+}
 
 constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest tile input (n=255: 8160 B; n=31: 7936 B) + spare
 // Full tiles write their syndromes straight to global memory (each lane's run
@@ -217,17 +282,20 @@ __global__ void __launch_bounds__(WARPS * 32)
             const uint32_t k = p.n - p.m;
             const uint32_t cnt = tl.count & ~kFullTile;
             if (!full) {
-                // ragged tail of cnt < one chunk: copy it in with coalesced loads,
+                // ragged tail of cnt < one chunk: its whole 16-byte groups came
+                // with the stage's bulk copy (tl.bytes); load the last words,
                 // drop the input pad bits and zero-fill the chunk, so that the
                 // padding decodes to zero data bits and zero syndromes
                 const uint32_t iw = (cnt * p.n + 31) / 32, cw_words = cwords * p.n / 32 + 4;
                 const uint32_t tail_bits = (cnt * p.n) & 31u;
                 const uint32_t *src = p.in + tl.c0 * p.n / 32u;
-                for (uint32_t w = lane; w < cw_words; w += 32) {
+                const uint32_t have = tl.bytes / 4;  // words already in the stage
+                for (uint32_t w = have + lane; w < cw_words; w += 32) {
                     uint32_t v = w < iw ? src[w] : 0u;
                     if (w == iw - 1 && tail_bits != 0) v &= (1u << tail_bits) - 1u;
                     stage[w] = v;
                 }
+                if (lane == 0 && tail_bits != 0 && iw - 1 < have) stage[iw - 1] &= (1u << tail_bits) - 1u;
                 __syncwarp();
             }
             uint32_t e = 0;
@@ -382,7 +450,6 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
 {
     if (num_packets > 0 && table == nullptr) return HD_ERR_NULL;
     pk.resize(num_packets);
-    std::vector<DevTile> tails;
     uint64_t ntiles = 0;
     for (uint32_t i = 0; i < num_packets; ++i) {
         const hd_packet &q = table[i];
@@ -420,28 +487,21 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
     if (ntiles >= 0xFFFFFFF0ull) return HD_ERR_CAPACITY;
     tiles.clear();
     tiles.reserve(ntiles);
-    // full tiles grouped by n (long codes first), then every packet's tail
+    // tiles grouped by n (long codes first), each code's tails among its full tiles
     static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
-    for (uint32_t n : order) {
-        for (uint32_t i = 0; i < num_packets; ++i) {
-            const DevPacket &d = pk[i];
-            if (d.n != n) continue;
-            const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
-            // n = 3 has no chunk decoder: all its codewords take the generic path
-            const uint64_t nfull = n == 3 ? 0 : d.num_cw / chunk;
-            const uint64_t per = (uint64_t)batch_chunks(n);
-            for (uint64_t j = 0; j < nfull; j += per) {
-                const uint64_t c = std::min(per, nfull - j);
-                tiles.push_back(make_tile(d.in, d.out, d.syn, d.num_cw, n, d.m, d.syn_type, i, j * chunk,
-                                          (uint32_t)(c * chunk) | kFullTile, (uint32_t)(c * chunk * n / 8)));
-            }
-            for (uint64_t c = nfull * chunk; c < d.num_cw; c += kTailTile)
-                tails.push_back(make_tile(d.in, d.out, d.syn, d.num_cw, n, d.m, d.syn_type, i, c,
-                                          (uint32_t)std::min<uint64_t>(kTailTile, d.num_cw - c), 0u));
-        }
-    }
-    if (stats) stats->full_tiles = (uint32_t)tiles.size();
-    tiles.insert(tiles.end(), tails.begin(), tails.end());
+    uint32_t nfull_tiles = 0;
+    for (uint32_t n : order)
+        emit_code_tiles(
+            n, num_packets,
+            [&](uint32_t i) {
+                const DevPacket &d = pk[i];
+                return PacketView{d.in, d.out, d.syn, d.num_cw, d.n, d.m, d.syn_type};
+            },
+            [&](const DevTile &t) {
+                tiles.push_back(t);
+                if (t.count & kFullTile) ++nfull_tiles;
+            });
+    if (stats) stats->full_tiles = nfull_tiles;
     return HD_OK;
 }
 
@@ -801,32 +861,19 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
     unsigned char *dbase = g_noalloc_dev[dev];
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // host image: full tiles grouped by n (long codes first), then tails
+    // host image: tiles grouped by n (long codes first), each code's tails among its full tiles
     DevTile *ht = reinterpret_cast<DevTile *>(g_noalloc_host + kNoAllocTilesOff);
     uint32_t t = 0;
     static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
-    for (int pass = 0; pass < 2; ++pass)
-        for (uint32_t n : order)
-            for (uint32_t i = 0; i < num_packets; ++i) {
+    for (uint32_t n : order)
+        emit_code_tiles(
+            n, num_packets,
+            [&](uint32_t i) {
                 const hd_packet &q = table[i];
-                if (q.n != n) continue;
-                const uint32_t m = (uint32_t)code_m(n);
-                const uint32_t st_i = q.syndromes ? q.syn_type : 0u;
-                uint8_t *sy = static_cast<uint8_t *>(q.syndromes);
-                const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
-                const uint64_t nfull = n == 3 ? 0 : q.num_codewords / chunk, per = (uint64_t)batch_chunks(n);
-                if (pass == 0) {
-                    for (uint64_t j = 0; j < nfull; j += per) {
-                        const uint64_t c = std::min(per, nfull - j);
-                        ht[t++] = make_tile(q.in, q.out, sy, q.num_codewords, n, m, st_i, i, j * chunk,
-                                            (uint32_t)(c * chunk) | kFullTile, (uint32_t)(c * chunk * n / 8));
-                    }
-                } else {
-                    for (uint64_t c = nfull * chunk; c < q.num_codewords; c += kTailTile)
-                        ht[t++] = make_tile(q.in, q.out, sy, q.num_codewords, n, m, st_i, i, c,
-                                            (uint32_t)std::min<uint64_t>(kTailTile, q.num_codewords - c), 0u);
-                }
-            }
+                return PacketView{q.in, q.out, static_cast<uint8_t *>(q.syndromes), q.num_codewords, q.n,
+                                  (uint32_t)code_m(q.n), q.syndromes ? q.syn_type : 0u};
+            },
+            [&](const DevTile &tile) { ht[t++] = tile; });
 
     // the claim counter must start at zero; the error counters are overwritten
     uint32_t *counter = reinterpret_cast<uint32_t *>(dbase);

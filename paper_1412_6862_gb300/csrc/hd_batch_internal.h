@@ -49,8 +49,8 @@ inline DevTile make_tile(const uint32_t *in, uint32_t *out, uint8_t *syn, uint64
     return t;
 }
 
-// Validate a packet table and cut it into tiles (full chunks grouped by n,
-// long codes first, then the ragged tails).  Adds the packets' algorithmic
+// Validate a packet table and cut it into tiles (grouped by n, long codes
+// first, each code's ragged tails spread among its full tiles).  Adds the packets' algorithmic
 // bytes (input + output + syndromes) to *bytes when not NULL.
 hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::vector<DevTile> &tiles,
                            uint64_t *bytes);
