@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--codes", type=str, default=",".join(map(str, SWEEP_CODES)),
                     help="subset of the sweep codes to run (profiling a single kernel)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adt", action="store_true", help="skip the SDT vs ADT (Eq. 1) transfer section")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in kernel configurations (the sweep autotunes each code by default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched mixed-n section")
@@ -608,6 +609,83 @@ def run_serving(dev, args, pool=None):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+ADT_CHUNK = 1 << 21  # codewords per packet of the transfer model (the host pipeline's chunk)
+
+
+def run_adt(bufs, codes, reps=5):
+    """The paper's synchronous vs asynchronous data transfer (Sec. III-B, Eq. 1) on
+    each sweep stream: the stream is cut into N packets of ADT_CHUNK codewords.
+    SDT = every packet's host-to-device copy, decode and device-to-host copy back
+    to back on one stream (CUDA events between the stages give the per-packet
+    T_PS, T_DKE and T_PR); ADT = hd_decode_host, the library's overlapped
+    pipeline, on the whole stream.  Eq. 1 predicts N(T_PS+T_DKE+T_PR) /
+    (T_PS + N T_DKE + T_PR), which assumes the kernel is the slowest stage; the
+    same pipeline with the slowest stage S = max(T_PS, T_DKE, T_PR) in that place
+    gives N(T_PS+T_DKE+T_PR) / (T_PS + T_DKE + T_PR + (N-1) S)."""
+    import torch
+    from paper_1412_6862_gb300 import hd
+    st = torch.cuda.Stream()
+    res = {}
+    for n in codes:
+        b = bufs[n]
+        N, k = b["N"], b["k"]
+        npk = N // ADT_CHUNK
+        iw, ow = ADT_CHUNK * n // 32, ADT_CHUNK * k // 32
+        d_in, out, syn, err = b["d_in"], b["out"], b["syn"], b["err"]
+        pinned, out_h, syn_h = b["pinned"], b["out_h"], b["syn_h"]
+        stage = {"ps": [], "dke": [], "pr": []}
+        sdt = []
+        for r in range(reps + 1):  # the first round warms up
+            evs = []
+            with torch.cuda.stream(st):
+                for c in range(npk):
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                    e[0].record(st)
+                    d_in[c * iw:(c + 1) * iw].copy_(pinned[c * iw:(c + 1) * iw], non_blocking=True)
+                    e[1].record(st)
+                    rc = hd.hd_decode(d_in.data_ptr() + 4 * c * iw, ADT_CHUNK * n, n, ADT_CHUNK,
+                                      out.data_ptr() + 4 * c * ow, syn.data_ptr() + c * ADT_CHUNK, hd.SYN_U8,
+                                      err.data_ptr(), st.cuda_stream)
+                    if rc != 0:
+                        raise hd.HDError(rc, "hd_decode")
+                    e[2].record(st)
+                    out_h[c * ow:(c + 1) * ow].copy_(out[c * ow:(c + 1) * ow], non_blocking=True)
+                    syn_h[c * ADT_CHUNK:(c + 1) * ADT_CHUNK].copy_(syn[c * ADT_CHUNK:(c + 1) * ADT_CHUNK],
+                                                                   non_blocking=True)
+                    e[3].record(st)
+                    evs.append(e)
+            st.synchronize()
+            if r == 0:
+                continue
+            sdt.append(evs[0][0].elapsed_time(evs[-1][3]) / 1e3)
+            for e in evs:
+                stage["ps"].append(e[0].elapsed_time(e[1]) / 1e3)
+                stage["dke"].append(e[1].elapsed_time(e[2]) / 1e3)
+                stage["pr"].append(e[2].elapsed_time(e[3]) / 1e3)
+        adt = []
+        for r in range(reps + 1):
+            t0 = time.perf_counter()
+            rc, _ = hd.hd_decode_host(b["pinned"].data_ptr(), N * n, n, N, out_h.data_ptr(), syn_h.data_ptr(),
+                                      hd.SYN_U8)
+            if rc != 0:
+                raise hd.HDError(rc, "hd_decode_host")
+            if r > 0:
+                adt.append(time.perf_counter() - t0)
+        t_ps, t_dke, t_pr = (float(np.median(stage[x])) for x in ("ps", "dke", "pr"))
+        t_sdt, t_adt = float(np.median(sdt)), float(np.median(adt))
+        slowest = max(t_ps, t_dke, t_pr)
+        res[str(n)] = {
+            "packets": npk, "codewords_per_packet": ADT_CHUNK,
+            "t_ps_us": t_ps * 1e6, "t_dke_us": t_dke * 1e6, "t_pr_us": t_pr * 1e6,
+            "sdt_ms": t_sdt * 1e3, "adt_ms": t_adt * 1e3, "speedup": t_sdt / t_adt,
+            "eq1_prediction": npk * (t_ps + t_dke + t_pr) / (t_ps + npk * t_dke + t_pr),
+            "slowest_stage_prediction": npk * (t_ps + t_dke + t_pr) / (t_ps + t_dke + t_pr + (npk - 1) * slowest),
+        }
+    return {"workload": "each sweep stream as N packets of 2^21 codewords: SDT (copy in, decode, copy out, "
+                        "per packet, one stream) vs ADT (hd_decode_host, overlapped pipeline); medians of "
+                        f"{reps} runs; host buffers pinned", "codes": res}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_setup(args.gpus)
@@ -777,6 +855,7 @@ def run_ours(args):
     barrier()
     e2e_s = reduce_max(max(time.perf_counter() - t0, 1e-9), dev)
     e2e_value = weak_scaling_value(bits_per_step * e2e_steps, world, e2e_s) / 1e9 if e2e_steps else None
+    adt = None if (args.no_adt or args.no_e2e) else run_adt(bufs, codes)
 
     batched = serving = None
     if not (args.no_batched and args.no_serve):
@@ -825,6 +904,7 @@ def run_ours(args):
             "serving": serving,
             "shortened": shortened,
             "secded": secded,
+            "adt": adt,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
