@@ -666,7 +666,7 @@ def run_adt(bufs, codes, reps=5):
         for r in range(reps + 1):
             t0 = time.perf_counter()
             rc, _ = hd.hd_decode_host(b["pinned"].data_ptr(), N * n, n, N, out_h.data_ptr(), syn_h.data_ptr(),
-                                      hd.SYN_U8)
+                                      hd.SYN_U8, ADT_CHUNK)
             if rc != 0:
                 raise hd.HDError(rc, "hd_decode_host")
             if r > 0:

@@ -82,7 +82,7 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
 
 /* Decode from and to HOST memory with overlapped transfers -- the paper's
  * asynchronous data transfer (Sec. III-B, Fig. 5, Eq. 1).  The stream is cut
- * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^21) and each
+ * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^22) and each
  * chunk's host-to-device copy, decode and device-to-host copy run on one of
  * `depth` CUDA streams (0 = 4, at most 8), so copies in both directions
  * overlap with the decoding of neighbouring chunks.  Arguments and results are
@@ -101,7 +101,7 @@ hd_status hd_decode_host(const uint32_t *host_stream, uint64_t in_bits, uint32_t
  * names a host stream of num_codewords codewords of length n and its host
  * outputs, as the arguments of hd_decode_host (pinned memory for overlap);
  * *host_err_count (or NULL) receives the job's number of nonzero syndromes.
- * All jobs' chunks (chunk_codewords, a multiple of 128; 0 = 2^21) go through
+ * All jobs' chunks (chunk_codewords, a multiple of 128; 0 = 2^22) go through
  * `depth` rotating CUDA streams (0 = 4, at most 8); the first chunks of the
  * batch ramp up from chunk/8 and the last ones ramp down, so the pipeline
  * fills and drains on small copies.  Synchronous; errors as hd_decode_host. */
