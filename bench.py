@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--batched-only", action="store_true", help="run only the batched mixed-n section")
     ap.add_argument("--batched-packets", type=int, default=10000)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--batched-config", type=int, default=-1,
+                    help="pin batch-kernel configuration I instead of hd_plan_autotune (e.g. for ncu)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-packets", type=int, default=100000)
@@ -372,7 +374,11 @@ def run_batched(dev, args, peak, keep_pool=False):
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     plan = hd.hd_plan_create(table, P)
-    tuned = hd.hd_plan_autotune(plan, 2, stream)
+    if args.batched_config >= 0:
+        hd.hd_plan_select(plan, args.batched_config)
+        tuned = hd.hd_plan_get_info(plan)
+    else:
+        tuned = hd.hd_plan_autotune(plan, 2, stream)
     setup_s = time.perf_counter() - t_setup
 
     def timed(fn, reps):

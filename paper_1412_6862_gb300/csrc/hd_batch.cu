@@ -2,9 +2,10 @@
 // persistent launch.
 //
 // A plan turns the packet table into a device table of tiles: every packet is
-// cut into full warp chunks of 32*G codewords (G = 32 for n <= 63, 16 for
-// n = 127, 8 for n = 255, so a chunk's input is at most 8 KB) and, when its
-// length is not a multiple of that, one ragged tail tile.  Warps of a
+// cut into full warp chunks of 32*G codewords (G = 32 for n <= 31, 16 for
+// n = 63, 8 for n = 127; n = 255 takes half-warp chunks of 16*8, so a chunk's
+// input is at most 4 KB) and, when its length is not a multiple of that, one
+// ragged tail tile.  Warps of a
 // persistent kernel claim tiles from an atomic counter in table order (tiles
 // grouped by n, each code's tails spread among its full tiles), prefetch
 // claimed tiles into their own shared-memory stages with 1-D bulk copies,
@@ -44,12 +45,22 @@ struct DevPacket {
 // than one chunk anyway; n = 3 streams are all tail).
 constexpr uint64_t kTailTile = 1024;
 
-__host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 255 ? 8 : (n >= 127 ? 16 : 32); }
+__host__ __device__ constexpr int batch_G(uint32_t n) { return n >= 127 ? 8 : (n >= 63 ? 16 : 32); }
+
+// Lanes of a chunk: n = 255 decodes half-warp chunks (128 codewords, 4080
+// bytes), so that every chunk's input fits a 4 KB stage.
+__host__ __device__ constexpr int batch_lanes(uint32_t n) { return n >= 255 ? 16 : 32; }
+
+// Codewords per chunk.
+__host__ __device__ constexpr uint64_t batch_chunk_cw(uint32_t n)
+{
+    return (uint64_t)batch_G(n) * (uint64_t)batch_lanes(n);
+}
 
 // Chunks per full tile: small codes pack several chunks (at most 4096
 // codewords) so that every tile moves several KB and the per-tile overhead
 // and load latency are amortised.
-__host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 15 ? 4 : (n <= 31 ? 2 : 1); }
+__host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 7 ? 4 : (n <= 15 ? 2 : 1); }
 
 // One packet as the tile builders see it.
 struct PacketView {
@@ -68,7 +79,7 @@ struct PacketView {
 template <class View, class Emit>
 void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit)
 {
-    const uint64_t chunk = 32ull * (uint64_t)batch_G(n);
+    const uint64_t chunk = batch_chunk_cw(n);
     const uint64_t per = (uint64_t)batch_chunks(n);
     auto nfull_of = [&](const PacketView &p) { return n == 3 ? 0 : p.num_cw / chunk; };  // n = 3: all tail
     uint64_t nf = 0, nt = 0;  // full tiles and tail tiles of this n
@@ -115,7 +126,10 @@ void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit)
     while (next_tail()) ++done_tail;
 }
 
-constexpr uint32_t kBatchStageBytes = 8192 + 16;  // largest tile input (n=255: 8160 B; n=31: 7936 B) + spare
+// Largest tile input (n = 255 half chunk: 4080 B; n = 127: 4064; n = 63: 4032;
+// n = 31: 3968; n = 15, two chunks: 3840; n = 7, four: 3584) plus a spare
+// group for the funnel read; 4 KB stages let 16 one-warp CTAs share an SM.
+constexpr uint32_t kBatchStageBytes = 4096 + 16;
 // Full tiles write their syndromes straight to global memory (each lane's run
 // of G syndromes is contiguous); only a ragged tail, at most one chunk, stages
 // them here before the copy that keeps within the packet.
@@ -150,10 +164,10 @@ template <int N_, int SYN, bool LUT>
 __device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sdst, int lane, uint32_t chunks,
                                                 const uint16_t *lut)
 {
-    using Q = ChunkGeom<N_, SYN, batch_G(N_)>;
+    using Q = ChunkGeom<N_, SYN, batch_G(N_), false, batch_lanes(N_)>;
     uint32_t e = 0, unused = 0;
     for (uint32_t c = 0; c < chunks; ++c)
-        e += decode_warp_chunk<N_, SYN, batch_G(N_), false, LUT>(stage + c * Q::in_words,
+        e += decode_warp_chunk<N_, SYN, batch_G(N_), false, LUT, batch_lanes(N_)>(stage + c * Q::in_words,
                                                                   const_cast<uint32_t *>(stage) + c * Q::out_words,
                                                                   sdst + c * Q::syn_bytes, lane, unused, lut);
     return e;
@@ -171,7 +185,7 @@ __device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uin
     }
 }
 
-__device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return 32u * (uint32_t)batch_G(n); }
+__device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return (uint32_t)batch_chunk_cw(n); }
 
 // lut7 (or nullptr: arithmetic decode) and, with T15, lut15 (required) are
 // the global decode tables of n = 7 and 15; the kernel copies them into shared
@@ -411,9 +425,9 @@ static const std::vector<BatchVariant> &batch_variants()
     // index 0 is the built-in choice (and the serving and allocation-free
     // paths' configuration); it holds no n = 15 table
     static const std::vector<BatchVariant> v = {
-        make_batch_variant<1, 2>(),       make_batch_variant<1, 3>(),       make_batch_variant<2, 2>(),
-        make_batch_variant<2, 3>(),       make_batch_variant<4, 2>(),       make_batch_variant<8, 2, true>(),
-        make_batch_variant<6, 2, true>(), make_batch_variant<6, 3, true>(), make_batch_variant<4, 3, true>()};
+        make_batch_variant<1, 3>(),        make_batch_variant<1, 2>(),        make_batch_variant<1, 4>(),
+        make_batch_variant<2, 2>(),        make_batch_variant<4, 2>(),        make_batch_variant<8, 2, true>(),
+        make_batch_variant<12, 2, true>(), make_batch_variant<14, 2, true>()};
     return v;
 }
 
@@ -473,7 +487,7 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
         d.in_words = words_for_bits(q.num_codewords * q.n);
         d.out_words = words_for_bits(q.num_codewords * (q.n - (uint32_t)m));
         d.pad = 0;
-        const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
+        const uint64_t chunk = batch_chunk_cw(q.n);
         const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
         const uint64_t per = (uint64_t)batch_chunks(q.n);
         ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
@@ -850,7 +864,7 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
             if (!aligned16(q.in) || !aligned16(q.out) || (q.syn_type != 0 && !aligned16(q.syndromes)))
                 return HD_ERR_ALIGN;
         }
-        const uint64_t chunk = 32ull * (uint64_t)batch_G(q.n);
+        const uint64_t chunk = batch_chunk_cw(q.n);
         const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
         const uint64_t per = (uint64_t)batch_chunks(q.n);
         ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;

@@ -42,14 +42,15 @@ struct StreamVariant {
     int lut = 0;  // decode table (n = 7, 15): one shared-memory lookup per codeword
 };
 
-// Geometry of one warp chunk of code n: 32*G codewords, G tiles of 32.  XH:
-// SECDED codewords of L = n + 1 bits (32 of them fill L words).
-template <int N_, int SYN, int G, bool XH = false>
+// Geometry of one warp chunk of code n: LANES*G codewords (LANES = 32, or 16
+// for a half-warp chunk), LANES*G/32 tiles of 32.  XH: SECDED codewords of
+// L = n + 1 bits (32 of them fill L words).
+template <int N_, int SYN, int G, bool XH = false, int LANES = 32>
 struct ChunkGeom {
     using C = Code<N_>;
     static constexpr int L = N_ + (XH ? 1 : 0);                       // input bits per codeword
     static constexpr int H = 32 / G;                                  // threads per 32-codeword tile
-    static constexpr int TEAMS = G;                                   // tiles per warp chunk
+    static constexpr int TEAMS = LANES / H;                           // tiles per warp chunk
     static constexpr int SB = SYN == 2 ? 2 : 1;                       // syndrome bytes (packing width)
     static constexpr bool WIDE = (SB == 1 && C::m + (XH ? 1 : 0) == 8);  // u8 lanes may use bit 7
     static constexpr int GK = G * C::k;                               // output bits per thread
@@ -68,7 +69,8 @@ struct ChunkGeom {
     static_assert(!PADDED || (R % 4 == 0 && 32 * R == (int)in_words), "padded parts are whole 16-byte groups");
     static constexpr uint32_t out_words = TEAMS * C::k;
     static constexpr uint32_t out_bytes = out_words * 4;
-    static constexpr uint32_t syn_bytes = SYN ? 32 * G * SB : 0;
+    static constexpr uint32_t syn_bytes = SYN ? LANES * G * SB : 0;
+    static_assert(LANES == 32 || (LANES == 16 && !PADDED && H <= 16), "whole tiles on the active lanes");
     static constexpr int V = !ALIGNED                                ? 1
                              : (C::k % 4 == 0 && (GK / 32) % 4 == 0) ? 4
                              : (C::k % 2 == 0 && (GK / 32) % 2 == 0) ? 2
@@ -80,12 +82,15 @@ struct ChunkGeom {
 // plus one spare word).  Writes the chunk's output words at `obase` (which may
 // equal `stage`: every lane copies its part to registers and the warp
 // synchronises before the first write) and its syndromes at `sbase`.  Returns
-// this lane's count of nonzero syndromes.
-template <int N_, int SYN, int G, bool XH = false, bool LUT = false>
+// this lane's count of nonzero syndromes.  With LANES = 16 the chunk is half
+// as long: lanes 16..31 read and write nothing (they only join the warp's
+// synchronisation) and return 0.
+template <int N_, int SYN, int G, bool XH = false, bool LUT = false, int LANES = 32>
 __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uint32_t *obase, uint8_t *sbase, int lane,
                                                       uint32_t &det, const uint16_t *lut = nullptr)
 {
-    using Q = ChunkGeom<N_, SYN, G, XH>;
+    using Q = ChunkGeom<N_, SYN, G, XH, LANES>;
+    const bool active = LANES == 32 || lane < LANES;
     constexpr int H = Q::H;
     const int team = lane / H, h = lane % H;
     const uint32_t in_bit = (uint32_t)h * (uint32_t)(G * Q::L);
@@ -93,7 +98,11 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
     const uint32_t out_bit = (uint32_t)h * (uint32_t)Q::GK;
     const uint32_t out_w = team * Code<N_>::k + (out_bit >> 5), out_sh = out_bit & 31u;
     uint32_t r[Q::R];
-    if constexpr (Q::PADDED) {
+    if (!active) {
+        // no part: keep the registers defined, never used
+#pragma unroll
+        for (int w = 0; w < Q::R; ++w) r[w] = 0u;
+    } else if constexpr (Q::PADDED) {
         const uint4 *part = reinterpret_cast<const uint4 *>(stage + lane * Q::part_words);
 #pragma unroll
         for (int t = 0; t < Q::R / 4; ++t) {
@@ -116,6 +125,7 @@ __device__ __forceinline__ uint32_t decode_warp_chunk(const uint32_t *stage, uin
         }
     }
     __syncwarp();  // the whole chunk is in registers
+    if (!active) return 0u;
     OutPacker<Q::GK, Q::ALIGNED, Q::V> op(obase + out_w, out_sh);
     SynPacker<Q::SB, SYN != 0, G, Q::WIDE> sp(sbase + (uint32_t)lane * G * Q::SB);
     decode_part<N_, G, Q::R, XH, LUT>(r, op, sp, det, lut);
