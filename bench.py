@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-adt", action="store_true", help="skip the SDT vs ADT (Eq. 1) transfer section")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in kernel configurations (the sweep autotunes each code by default)")
+    ap.add_argument("--pin", type=str, default="",
+                    help="n:i,... pin configuration i of code n (u8 syndromes) instead of autotuning it (for ncu)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched mixed-n section")
     ap.add_argument("--batched-only", action="store_true", help="run only the batched mixed-n section")
     ap.add_argument("--batched-packets", type=int, default=10000)
@@ -113,16 +115,19 @@ def kernel_sources_hash():
 
 
 def recorded_traffic(kernel_desc):
-    """DRAM bytes per launch of the roofline kernel from the committed ncu record,
-    or None when the kernel sources or its configuration changed since."""
+    """DRAM bytes per launch of the roofline kernel from the committed ncu records
+    (one per configuration the autotuner may choose), or None when no record is
+    for this configuration or the kernel sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic_n63.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        rec = json.load(f)
-    if rec.get("sources_sha256") != kernel_sources_hash() or rec.get("kernel") != kernel_desc:
-        return None
-    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+        recs = json.load(f).get("records", [])
+    h = kernel_sources_hash()
+    for rec in recs:
+        if rec.get("sources_sha256") == h and rec.get("kernel") == kernel_desc:
+            return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    return None
 
 
 def reduce_max(value, device=None):
@@ -758,12 +763,18 @@ def run_ours(args):
     # sweep's size on random data streamed from HBM (outside the timed region)
     # and keeps the fastest, unless the built-in one is within its noise margin
     tuned = {}
-    if not args.no_autotune:
-        for n in codes:
+    pins = dict(tuple(int(v) for v in item.split(":")) for item in args.pin.split(",")) if args.pin else {}
+    for n in codes:
+        if n in pins:
+            hd.hd_variant_select(n, hd.SYN_U8, pins[n])
+            info = hd.hd_variant_current(n, hd.SYN_U8)
+        elif not args.no_autotune:
             info = hd.hd_autotune(n, hd.SYN_U8, SWEEP_N, 5, stream_h)
-            tuned[str(n)] = {key: info[key] for key in ("threads", "stages", "codewords_per_thread", "inplace",
-                                                        "table_lookup")}
-        torch.cuda.synchronize()
+        else:
+            continue
+        tuned[str(n)] = {key: info[key] for key in ("threads", "stages", "codewords_per_thread", "inplace",
+                                                    "table_lookup")}
+    torch.cuda.synchronize()
 
     def decode_call(n, cuda_stream):
         b = bufs[n]
