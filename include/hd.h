@@ -315,7 +315,10 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
  * of num_packets elements, or NULL; element i is overwritten with packet i's
  * number of nonzero syndromes.  The first launch (and any launch with a
  * different err_counts pointer) records the launch as a CUDA graph; later
- * launches replay it. */
+ * launches replay it.  n = 7 packets decode with a 256-byte table that the
+ * first batched decode on a device fills on `cuda_stream` and then
+ * synchronises it (a launch whose stream is capturing before that decodes
+ * n = 7 arithmetically). */
 hd_status hd_plan_launch(hd_plan *plan, unsigned long long *err_counts, void *cuda_stream);
 
 /* Time every batch-kernel configuration on the plan's own packets (`reps`
@@ -332,7 +335,8 @@ void hd_plan_destroy(hd_plan *plan);
 
 /* One-shot batched decode: builds the device tables in stream-ordered memory
  * (cudaMallocAsync, freed with cudaFreeAsync after the launch), decodes and
- * overwrites err_counts (device, num_packets elements, or NULL). */
+ * overwrites err_counts (device, num_packets elements, or NULL).  The n = 7
+ * table is filled on first use as for hd_plan_launch(). */
 hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
                           void *cuda_stream);
 
@@ -345,9 +349,10 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
  * tile) and claim counter live in one fixed 1 MiB array compiled into libhd.so; every device that
  * loads the library holds that array until the process exits.
  *
- * Limits: at most 4096 packets and 16,380 tiles (a tile is one to four chunks of 256 to
- * 1024 codewords, or up to 1024 codewords of a packet's tail); larger batches
- * return HD_ERR_CAPACITY before anything is enqueued.
+ * Limits: at most 4096 packets and 16,380 tiles (a tile is one to four chunks of 128 to
+ * 1024 codewords, at most 4 KB of input, or a packet's tail); larger batches
+ * return HD_ERR_CAPACITY before anything is enqueued.  This path decodes n = 7
+ * without the decode table, so it never fills or synchronises anything.
  * First call on a device: performs a one-time set-up (it looks up the array's
  * device address and the kernel's launch attributes); make that first call
  * before any stream capture.
@@ -381,7 +386,7 @@ typedef struct hd_server hd_server;
 typedef struct {
     uint32_t max_waves;        /* wave slots (concurrent batched launches), 1..64 */
     uint32_t max_wave_packets; /* packets per wave */
-    uint32_t max_wave_tiles;   /* tile-table capacity per wave (a packet of N codewords needs <= N/256 + 2) */
+    uint32_t max_wave_tiles;   /* tile-table capacity per wave (a packet of N codewords needs <= N/128 + 1) */
     uint32_t queue_capacity;   /* submitted packets waiting for admission */
     uint64_t mem_cap_bytes;    /* admission budget in bytes (see above) */
 } hd_server_config;

@@ -62,6 +62,14 @@ __host__ __device__ constexpr uint64_t batch_chunk_cw(uint32_t n)
 // and load latency are amortised.
 __host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 7 ? 4 : (n <= 15 ? 2 : 1); }
 
+uint64_t packet_tiles(uint32_t n, uint64_t num_codewords)
+{
+    const uint64_t chunk = batch_chunk_cw(n);
+    const uint64_t nfull = n == 3 ? 0 : num_codewords / chunk;  // n = 3: all tail
+    const uint64_t per = (uint64_t)batch_chunks(n);
+    return (nfull + per - 1) / per + (num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+}
+
 // One packet as the tile builders see it.
 struct PacketView {
     const uint32_t *in;
@@ -487,10 +495,7 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
         d.in_words = words_for_bits(q.num_codewords * q.n);
         d.out_words = words_for_bits(q.num_codewords * (q.n - (uint32_t)m));
         d.pad = 0;
-        const uint64_t chunk = batch_chunk_cw(q.n);
-        const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
-        const uint64_t per = (uint64_t)batch_chunks(q.n);
-        ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+        ntiles += packet_tiles(q.n, q.num_codewords);
         if (stats) {
             stats->codewords += q.num_codewords;
             stats->in_bytes += (q.num_codewords * q.n + 7) / 8;
@@ -864,10 +869,7 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
             if (!aligned16(q.in) || !aligned16(q.out) || (q.syn_type != 0 && !aligned16(q.syndromes)))
                 return HD_ERR_ALIGN;
         }
-        const uint64_t chunk = batch_chunk_cw(q.n);
-        const uint64_t nfull = q.n == 3 ? 0 : q.num_codewords / chunk;
-        const uint64_t per = (uint64_t)batch_chunks(q.n);
-        ntiles += (nfull + per - 1) / per + (q.num_codewords - nfull * chunk + kTailTile - 1) / kTailTile;
+        ntiles += packet_tiles(q.n, q.num_codewords);
     }
     if (ntiles > kNoAllocMaxTiles) return HD_ERR_CAPACITY;
     const hd_status su = noalloc_setup(dev);

@@ -49,6 +49,10 @@ inline DevTile make_tile(const uint32_t *in, uint32_t *out, uint8_t *syn, uint64
     return t;
 }
 
+// Exact number of tiles the batch plan cuts a packet of code length n and
+// num_codewords codewords into (n must be a supported length).
+uint64_t packet_tiles(uint32_t n, uint64_t num_codewords);
+
 // Validate a packet table and cut it into tiles (grouped by n, long codes
 // first, each code's ragged tails spread among its full tiles).  Adds the packets' algorithmic
 // bytes (input + output + syndromes) to *bytes when not NULL.

@@ -54,8 +54,7 @@ bool packet_cost(const hd_packet &q, uint64_t *bytes, uint64_t *tiles, hd_status
     }
     const uint64_t N = q.num_codewords, k = q.n - (uint32_t)m;
     *bytes = (N * q.n + 7) / 8 + (N * k + 7) / 8 + N * (q.syn_type == 2 ? 2 : (q.syn_type == 1 ? 1 : 0));
-    // a generous bound on the tiles the batch plan cuts this packet into
-    *tiles = N / 256 + 2;
+    *tiles = packet_tiles(q.n, N);  // exactly as the batch plan cuts it
     return true;
 }
 

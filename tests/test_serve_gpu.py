@@ -108,3 +108,32 @@ def test_drain_waits_for_every_admitted_packet():
             assert rc == hd.HD_OK and len(comps) == len(pk), (rep, len(comps))
         finally:
             srv.close()
+
+
+def test_wave_tile_limit_counts_short_chunks_exactly():
+    # n = 255 packets of 7,680 codewords are exactly 60 tiles each (half-warp
+    # chunks of 128 codewords), so a 64-tile wave holds one of them: admission
+    # must count the tiles as the batch plan cuts them, never two per wave
+    import torch
+    n, N = 255, 128 * 60
+    m, k = hd.code_params(n)
+    pk = []
+    for j in range(4):
+        stream, _, _ = gc.received_stream(n, N, seed=900 + j, p1=0.1, p2=0.02)
+        d_in = gc.to_device(stream)
+        alone = hd.decode(d_in, n, N, syn_type=hd.SYN_U16)
+        out = torch.full((hd.words_for(N * k),), -1, dtype=torch.int32, device="cuda")
+        syn = torch.full((N,), 0x77, dtype=torch.int16, device="cuda")
+        pk.append(dict(n=n, N=N, st=hd.SYN_U16, d_in=d_in, alone=alone, out=out, syn=syn))
+    torch.cuda.synchronize()
+    srv = hd.Server(hd.server_config(max_waves=2, max_wave_packets=8, max_wave_tiles=64, queue_capacity=16))
+    for j, p in enumerate(pk):
+        assert srv.submit(p["d_in"].data_ptr(), p["out"].data_ptr(), p["syn"].data_ptr(), N, n, p["st"], j) == hd.HD_OK
+    assert srv.drain(60.0) == hd.HD_OK
+    rc, comps = srv.poll(16)
+    assert rc == hd.HD_OK and len(comps) == len(pk)
+    assert srv.stats()["waves"] >= len(pk)  # one packet per wave
+    for c in comps:
+        assert c.status == hd.HD_OK
+        _same(pk[c.tag], c.err_count)
+    srv.close()
