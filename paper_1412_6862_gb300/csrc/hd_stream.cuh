@@ -58,12 +58,13 @@ struct ChunkGeom {
     static constexpr int R = (G * L + 31) / 32;                       // input words per thread after re-alignment
     static constexpr uint32_t in_words = TEAMS * L;
     static constexpr uint32_t in_bytes = in_words * 4;
-    // PADDED (SECDED with n >= 127): each thread's part (R words, whole codewords) has its own
+    // PADDED (SECDED with n >= 63): each thread's part (R words, whole codewords) has its own
     // stage slot of R + 4 words, loaded by its own bulk copy, so that 128-bit reads of the 32
     // parts fall on distinct banks (a part stride that is a multiple of 32 words would put every
-    // lane on the same bank).  For shorter SECDED codewords one bulk copy per chunk measured
-    // faster on GB300 despite the conflicts.
-    static constexpr bool PADDED = XH && N_ >= 127;
+    // lane on the same bank).  For n = 63 this measured 56 µs against 64 µs per 2^24
+    // codewords on GB300; for n <= 31 one bulk copy per chunk measured faster despite the
+    // conflicts (n = 31: 40 µs against 46).
+    static constexpr bool PADDED = XH && N_ >= 63;
     static constexpr uint32_t part_words = R + 4;
     static constexpr uint32_t stage_payload = PADDED ? 32 * part_words * 4 : in_bytes;
     static_assert(!PADDED || (R % 4 == 0 && 32 * R == (int)in_words), "padded parts are whole 16-byte groups");
