@@ -202,7 +202,10 @@ hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, v
  * bit itself, the data are intact); P = 0 with s != 0 is a detected double
  * error, left as received and counted in *detected_count.  Syndrome element i
  * is s | P << m (HD_SYN_U8 only for n <= 127); *err_count counts nonzero
- * elements.  Other arguments, layout, counters and errors as hd_decode(). */
+ * elements.  Other arguments, layout, counters and errors as hd_decode().
+ * n = 7 and 15 decode with a table (512 B / 128 KB of device memory) that the
+ * first such call on a device fills on `cuda_stream` and then synchronises it;
+ * a first call while the stream is capturing decodes arithmetically. */
 hd_status hd_decode_secded(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
                            uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
                            unsigned long long *err_count, unsigned long long *detected_count, void *cuda_stream);

@@ -182,16 +182,23 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
                                       uint64_t *covered)
 {
     *covered = 0;
-    const StreamVariant *v = nullptr;
+    // the table configuration when its table is filled (not while `st` captures
+    // before the first fill), else the arithmetic one
+    const StreamVariant *v = nullptr, *vt = nullptr;
     for (const StreamVariant &x : secded_variants())
-        if (x.n == n && x.syn == syn_type) v = &x;
+        if (x.n == n && x.syn == syn_type) {
+            if (!x.lut) v = &x;
+            else if (vt == nullptr) vt = &x;
+        }
+    const uint16_t *lut = vt != nullptr ? lut_ptr(n, st, true) : nullptr;
+    if (lut != nullptr) v = vt;
     if (v == nullptr) return cudaSuccess;
     const uint64_t nchunks = num_cw / v->chunk_cw;
     if (nchunks == 0) return cudaSuccess;
     uint32_t *status = status_ptr();
     if (status == nullptr) return cudaErrorInvalidSymbol;
     *covered = nchunks * v->chunk_cw;
-    return v->launch(*v, in, nchunks, out, syn, err, status, st, det, nullptr);
+    return v->launch(*v, in, nchunks, out, syn, err, status, st, det, v->lut ? lut : nullptr);
 }
 
 // ---------------------------------------------------------------------------

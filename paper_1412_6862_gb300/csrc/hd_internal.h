@@ -47,10 +47,11 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
                                       int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
                                       uint64_t *covered);
 
-// Decode table of n = 7 or 15 (data | s << k per codeword), filled on `st` on
-// first use per device; nullptr for other n, or when the table is not filled
-// yet and `st` is capturing.
-const uint16_t *lut_ptr(uint32_t n, cudaStream_t st);
+// Decode table of n = 7 or 15 (data | s << k per codeword; with xh the SECDED
+// table of n + 1 bits, data | s << k | P << (k + m)), filled on `st` on first
+// use per device; nullptr for other n, or when the table is not filled yet and
+// `st` is capturing.
+const uint16_t *lut_ptr(uint32_t n, cudaStream_t st, bool xh = false);
 
 // Device address of the status word that kernels latch HD_ERR_TIMEOUT into
 // (per device; nullptr on failure), and its host-side read-and-clear.

@@ -150,7 +150,7 @@ struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     static constexpr uint32_t off_in = 64;
     static constexpr uint32_t off_out = off_in + S * stage_bytes;
     static constexpr uint32_t warp_bytes = (off_out + (INPLACE ? 0 : 2 * out_buf_bytes) + 127) / 128 * 128;
-    static constexpr uint32_t lut_bytes = LUT ? (2u << N_) : 0u;  // u16 per codeword value
+    static constexpr uint32_t lut_bytes = LUT ? (2u << (N_ + (XH ? 1 : 0))) : 0u;  // u16 per codeword value
     static constexpr uint32_t off_lut = WARPS * warp_bytes;         // the table, then its mbarrier
     static constexpr uint32_t smem = off_lut + (LUT ? lut_bytes + 16u : 0u);
     static constexpr bool fits = smem <= 232448;  // the opt-in maximum per CTA

@@ -1,6 +1,7 @@
 // hd_stream_x.cu -- the SECDED configurations of the streaming decoder, one
 // per length n (codewords per thread, threads per CTA, stages, in-place), for
-// every syndrome type: the fastest of a sweep of configurations on GB300.
+// every syndrome type: the fastest of a sweep of configurations on GB300; for
+// n = 7 and 15 also one with the SECDED decode table.
 #include "hd_stream.cuh"
 
 namespace hd {
@@ -13,6 +14,9 @@ void register_stream_secded(std::vector<StreamVariant> &v)
     add_variants<63, 128, 2, 32, 1, true>(v);
     add_variants<127, 128, 2, 8, 1, true>(v);
     add_variants<255, 128, 2, 8, 1, true>(v);
+    // decode tables (one lookup per codeword; used when the table is filled)
+    add_variants<7, 128, 4, 32, 1, true, true>(v);
+    add_variants<15, 512, 2, 32, 1, true, true>(v);  // 128 KB table per CTA
 }
 
 }  // namespace hd

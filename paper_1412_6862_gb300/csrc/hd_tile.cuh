@@ -316,14 +316,16 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
 {
     using C = Code<N_>;
     if constexpr (LUT) {
-        // one lookup per codeword: its n bits index data | s << k.  All G
-        // lookups are issued before any result is packed, so their shared
-        // memory latencies overlap.
-        static_assert(N_ <= 15 && !XH, "decode tables exist for n = 7 and 15");
+        // one lookup per codeword: its n bits index data | s << k (SECDED: its
+        // n + 1 bits index data | s << k | P << (k + m)).  All G lookups are
+        // issued before any result is packed, so their shared-memory latencies
+        // overlap.
+        static_assert(N_ <= 15, "decode tables exist for n = 7 and 15");
+        constexpr int L = N_ + (XH ? 1 : 0);
         uint32_t e[G];
 #pragma unroll
         for (int c = 0; c < G; ++c) {
-            const int start = c * N_;  // a constant once the loop is unrolled
+            const int start = c * L;  // a constant once the loop is unrolled
             const int a = start >> 5, sh = start & 31;
             uint32_t v;
             if (sh == 0)
@@ -332,12 +334,14 @@ __device__ __forceinline__ void decode_part(const uint32_t (&r)[R], OP &op, SP &
                 v = __funnelshift_r(r[a], r[a + 1], sh);
             else
                 v = r[a] >> sh;
-            e[c] = lut[v & ((1u << N_) - 1u)];
+            e[c] = lut[v & ((1u << L) - 1u)];
         }
 #pragma unroll
         for (int c = 0; c < G; ++c) {
             op.append(e[c] & ((1u << C::k) - 1u), C::k);
-            sp.put(c, e[c] >> C::k);
+            const uint32_t sv = e[c] >> C::k;  // s, or for SECDED s | P << m
+            if constexpr (XH) det += (sv - 1u < (1u << C::m) - 1u) ? 1u : 0u;  // P = 0 and s != 0
+            sp.put(c, sv);
         }
     } else {
 #pragma unroll
