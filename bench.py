@@ -623,6 +623,21 @@ def run_serving(dev, args, pool=None):
 ADT_CHUNK = 1 << 21  # codewords per packet of the transfer model (the host pipeline's chunk)
 
 
+def eq1_speedup(npk, t_ps, t_dke, t_pr):
+    """Eq. 1: speedup of ADT over SDT for npk packets, N(T_PS+T_DKE+T_PR) /
+    (T_PS + N T_DKE + T_PR): the pipeline hides every packet's transfers behind
+    the kernels of the others, i.e. assumes the kernel is the slowest stage."""
+    return npk * (t_ps + t_dke + t_pr) / (t_ps + npk * t_dke + t_pr)
+
+
+def pipeline_speedup(npk, t_ps, t_dke, t_pr):
+    """The same three-stage pipeline with the slowest stage S = max(T_PS, T_DKE,
+    T_PR) setting the pace: N(T_PS+T_DKE+T_PR) / (T_PS+T_DKE+T_PR + (N-1) S).
+    Equals Eq. 1 when the kernel is the slowest stage."""
+    s = max(t_ps, t_dke, t_pr)
+    return npk * (t_ps + t_dke + t_pr) / (t_ps + t_dke + t_pr + (npk - 1) * s)
+
+
 def run_adt(bufs, codes, reps=5):
     """The paper's synchronous vs asynchronous data transfer (Sec. III-B, Eq. 1) on
     each sweep stream: the stream is cut into N packets of ADT_CHUNK codewords.
@@ -684,13 +699,12 @@ def run_adt(bufs, codes, reps=5):
                 adt.append(time.perf_counter() - t0)
         t_ps, t_dke, t_pr = (float(np.median(stage[x])) for x in ("ps", "dke", "pr"))
         t_sdt, t_adt = float(np.median(sdt)), float(np.median(adt))
-        slowest = max(t_ps, t_dke, t_pr)
         res[str(n)] = {
             "packets": npk, "codewords_per_packet": ADT_CHUNK,
             "t_ps_us": t_ps * 1e6, "t_dke_us": t_dke * 1e6, "t_pr_us": t_pr * 1e6,
             "sdt_ms": t_sdt * 1e3, "adt_ms": t_adt * 1e3, "speedup": t_sdt / t_adt,
-            "eq1_prediction": npk * (t_ps + t_dke + t_pr) / (t_ps + npk * t_dke + t_pr),
-            "slowest_stage_prediction": npk * (t_ps + t_dke + t_pr) / (t_ps + t_dke + t_pr + (npk - 1) * slowest),
+            "eq1_prediction": eq1_speedup(npk, t_ps, t_dke, t_pr),
+            "slowest_stage_prediction": pipeline_speedup(npk, t_ps, t_dke, t_pr),
         }
     return {"workload": "each sweep stream as N packets of 2^21 codewords: SDT (copy in, decode, copy out, "
                         "per packet, one stream) vs ADT (hd_decode_host, overlapped pipeline); medians of "
