@@ -369,6 +369,16 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
 hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
                                   void *cuda_stream);
 
+/* Number of tiles (the batch kernel's work items) the packets of `table` are
+ * cut into, in *tiles: the unit of hd_decode_batch_noalloc()'s capacity and of
+ * hd_server_config.max_wave_tiles.  A packet of N codewords of length n gives
+ * ceil(F / c) full tiles of c chunks plus ceil((N - F * chunk) / 1024) tail
+ * tiles, where chunk = 1024 codewords for n <= 31, 512 for n = 63, 256 for
+ * n = 127 and 128 for n = 255, F = floor(N / chunk) (0 for n = 3), and c = 4
+ * for n = 7, 2 for n = 15, else 1.  Host-only: checks n (HD_ERR_INVALID_N),
+ * syn_type (HD_ERR_INVALID_ARG) and sizes (HD_ERR_SIZE) but no pointers. */
+hd_status hd_batch_tiles(const hd_packet *table, uint32_t num_packets, uint64_t *tiles);
+
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of arriving packets.
  *

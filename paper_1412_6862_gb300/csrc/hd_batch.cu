@@ -848,6 +848,21 @@ hd_status noalloc_setup(int dev)
 }  // namespace
 }  // namespace hd
 
+extern "C" hd_status hd_batch_tiles(const hd_packet *table, uint32_t num_packets, uint64_t *tiles)
+{
+    if (tiles == nullptr || (num_packets > 0 && table == nullptr)) return HD_ERR_NULL;
+    uint64_t t = 0;
+    for (uint32_t i = 0; i < num_packets; ++i) {
+        const hd_packet &q = table[i];
+        if (code_m(q.n) == 0) return HD_ERR_INVALID_N;
+        if (q.syn_type > 2) return HD_ERR_INVALID_ARG;
+        if (q.num_codewords > (1ull << 40)) return HD_ERR_SIZE;
+        t += packet_tiles(q.n, q.num_codewords);
+    }
+    *tiles = t;
+    return HD_OK;
+}
+
 extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets,
                                              unsigned long long *err_counts, void *cuda_stream)
 {

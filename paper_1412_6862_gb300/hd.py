@@ -115,6 +115,7 @@ SIGNATURES = {
     "hd_plan_destroy": (None, [_vp]),
     "hd_decode_batch": (_i32, [_PKP, _u32, _vp, _vp]),
     "hd_decode_batch_noalloc": (_i32, [_PKP, _u32, _vp, _vp]),
+    "hd_batch_tiles": (_i32, [_PKP, _u32, _c.POINTER(_u64)]),
     "hd_server_create": (_i32, [_SCP, _c.POINTER(_vp)]),
     "hd_server_submit": (_i32, [_vp, _PKP, _u64]),
     "hd_server_poll": (_i32, [_vp, _CMP, _u32, _c.POINTER(_u32)]),
@@ -310,6 +311,13 @@ def hd_decode_batch(table, num_packets: int, err_counts, cuda_stream) -> int:
 
 def hd_decode_batch_noalloc(table, num_packets: int, err_counts, cuda_stream) -> int:
     return lib().hd_decode_batch_noalloc(table, num_packets, err_counts, cuda_stream)
+
+
+def hd_batch_tiles(table, num_packets: int) -> int:
+    """Tiles the packets are cut into (host-only)."""
+    t = _u64(0)
+    check(lib().hd_batch_tiles(table, num_packets, ctypes.byref(t)), "hd_batch_tiles")
+    return int(t.value)
 
 
 def server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=65536, queue_capacity=1 << 16,

@@ -167,3 +167,37 @@ def test_host_batch_validation_host_only(lib):
     assert hd.hd_decode_host_batch([(None, 15, 4, z.ctypes.data, None, 0)])[0] == hd.HD_ERR_NULL
     assert hd.hd_decode_host_batch([(z.ctypes.data, 15, 4, z.ctypes.data, None, 1)])[0] == hd.HD_ERR_NULL
     assert lib.hd_decode_host_batch(None, 1, 0, 0) == hd.HD_ERR_NULL
+
+
+def _tiles_model(n, N):
+    # the batch plan's cut: whole chunks grouped into full tiles, then tails of
+    # at most 1024 codewords (n = 3 is all tail)
+    chunk = {3: 1024, 7: 1024, 15: 1024, 31: 1024, 63: 512, 127: 256, 255: 128}[n]
+    per = {7: 4, 15: 2}.get(n, 1)
+    full = 0 if n == 3 else N // chunk
+    return -(-full // per) + -(-(N - full * chunk) // 1024)
+
+
+def test_batch_tiles_host_only(lib):
+    rng = np.random.default_rng(5)
+    codes = (3, 7, 15, 31, 63, 127, 255)
+    for trial in range(40):
+        P = int(rng.integers(0, 50))
+        rows = [(16, 16, None, int(rng.integers(0, 1 << int(rng.integers(0, 22)))), int(rng.choice(codes)), 0)
+                for _ in range(P)]
+        expected = sum(_tiles_model(n, N) for (_, _, _, N, n, _) in rows)
+        assert hd.hd_batch_tiles(hd.packet_table(rows), P) == expected
+    # worked cases: one chunk fewer or more changes the count as the rule says
+    assert hd.hd_batch_tiles(hd.packet_table([(16, 16, None, 128 * 60, 255, 0)]), 1) == 60
+    assert hd.hd_batch_tiles(hd.packet_table([(16, 16, None, 128 * 60 + 1, 255, 0)]), 1) == 61
+    assert hd.hd_batch_tiles(hd.packet_table([(16, 16, None, 4096 * 3, 7, 0)]), 1) == 3
+    assert hd.hd_batch_tiles(hd.packet_table([(16, 16, None, 0, 15, 0)]), 1) == 0
+    import ctypes
+    t = ctypes.c_uint64(0)
+    assert hd.lib().hd_batch_tiles(hd.packet_table([(16, 16, None, 10, 8, 0)]), 1, ctypes.byref(t)) == \
+        hd.HD_ERR_INVALID_N
+    assert hd.lib().hd_batch_tiles(hd.packet_table([(16, 16, None, 10, 7, 3)]), 1, ctypes.byref(t)) == \
+        hd.HD_ERR_INVALID_ARG
+    assert hd.lib().hd_batch_tiles(hd.packet_table([(16, 16, None, (1 << 40) + 1, 7, 0)]), 1, ctypes.byref(t)) == \
+        hd.HD_ERR_SIZE
+    assert hd.lib().hd_batch_tiles(None, 2, ctypes.byref(t)) == hd.HD_ERR_NULL
