@@ -267,6 +267,18 @@ hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *
 hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,
                       hd_variant_info *chosen);
 
+/* SECDED configurations.  hd_decode_secded() decodes whole chunks with one
+ * streaming configuration per (n, syn_type) and, for n = 7 and 15, a second
+ * one that decodes through the SECDED table; by default the table one is used
+ * once its table is filled.  hd_secded_variant_select() pins configuration
+ * `ordinal` (< count) for (n, syn_type) on the current device (ordinal < 0
+ * restores the default); a table configuration pinned while its table cannot
+ * be filled (a first call inside a stream capture) decodes arithmetically.
+ * The configuration never changes the result, only the speed.  Host only. */
+hd_status hd_secded_variant_count(uint32_t n, hd_syn_type syn_type, uint32_t *count);
+hd_status hd_secded_variant_info_get(uint32_t n, hd_syn_type syn_type, uint32_t ordinal, hd_variant_info *info);
+hd_status hd_secded_variant_select(uint32_t n, hd_syn_type syn_type, int32_t ordinal);
+
 /* ---------------------------------------------------------------------------
  * Batched decode: many packets of mixed n and length in one persistent launch.
  *
@@ -463,6 +475,19 @@ hd_status hd_device_status(uint32_t *status);
 /* Number of kernels this library has launched in this process (a host-side
  * counter, incremented once per kernel launch it enqueues). */
 uint64_t hd_launch_count(void);
+
+/* Cap the number of CTAs (thread blocks) of every decode launch that this
+ * library enqueues from now on, on every device: max_ctas = 0 (the default)
+ * removes the cap.  The persistent kernels then give each warp more chunks or
+ * tiles to walk through; results never change.  Uses: leaving SMs free for
+ * other kernels that run beside the decoder, and tests that make every warp's
+ * staging ring wrap many times on inputs small enough for the CPU oracle.
+ * Launch geometry already recorded in a CUDA graph (a plan's graph, recorded
+ * on its first launch) keeps its grid.  Host only; always HD_OK. */
+hd_status hd_set_max_ctas(uint32_t max_ctas);
+
+/* The cap set by hd_set_max_ctas() (0 = none). */
+uint32_t hd_get_max_ctas(void);
 
 /* Library version, major*10000 + minor*100 + patch. */
 int hd_version(void);

@@ -8,6 +8,7 @@
 namespace hd {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint32_t> g_max_ctas{0};
 
 int num_sms()
 {
@@ -41,6 +42,14 @@ extern "C" {
 int hd_version(void) { return 100; }
 
 uint64_t hd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+hd_status hd_set_max_ctas(uint32_t max_ctas)
+{
+    g_max_ctas.store(max_ctas, std::memory_order_relaxed);
+    return HD_OK;
+}
+
+uint32_t hd_get_max_ctas(void) { return g_max_ctas.load(std::memory_order_relaxed); }
 
 const char *hd_status_string(hd_status status)
 {

@@ -530,7 +530,7 @@ int batch_grid(const BatchVariant &v, uint32_t num_tiles)
     if (bps <= 0) return -1;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = ((uint64_t)num_tiles + v.warps - 1) / v.warps;
-    return (int)std::max<uint64_t>(1, std::min(cap, want));
+    return decode_grid(want, cap);
 }
 
 // Resolve everything that touches device state before a (possibly captured)

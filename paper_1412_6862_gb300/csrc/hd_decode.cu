@@ -69,6 +69,8 @@ int current_device()
 std::map<std::pair<int, const void *>, int> g_bps;
 // (device, n, syn) -> chosen variant index (autotuner or explicit selection)
 std::map<std::tuple<int, uint32_t, int>, int> g_choice;
+// (device, n, syn) -> pinned SECDED configuration (index into secded_variants())
+std::map<std::tuple<int, uint32_t, int>, int> g_secded_choice;
 // device -> address of g_hd_status
 std::map<int, uint32_t *> g_status_ptr;
 
@@ -182,14 +184,29 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
                                       uint64_t *covered)
 {
     *covered = 0;
-    // the table configuration when its table is filled (not while `st` captures
-    // before the first fill), else the arithmetic one
+    // a pinned configuration (hd_secded_variant_select), else the table
+    // configuration when its table is filled (not while `st` captures before
+    // the first fill), else the arithmetic one
     const StreamVariant *v = nullptr, *vt = nullptr;
     for (const StreamVariant &x : secded_variants())
         if (x.n == n && x.syn == syn_type) {
-            if (!x.lut) v = &x;
-            else if (vt == nullptr) vt = &x;
+            if (!x.lut) {
+                if (v == nullptr) v = &x;
+            } else if (vt == nullptr) {
+                vt = &x;
+            }
         }
+    int pinned = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_secded_choice.find({current_device(), n, syn_type});
+        if (it != g_secded_choice.end()) pinned = it->second;
+    }
+    if (pinned >= 0) {
+        const StreamVariant &x = secded_variants()[pinned];
+        if (x.lut) vt = &x;
+        else v = &x, vt = nullptr;
+    }
     const uint16_t *lut = vt != nullptr ? lut_ptr(n, st, true) : nullptr;
     if (lut != nullptr) v = vt;
     if (v == nullptr) return cudaSuccess;
@@ -295,6 +312,66 @@ hd_status hd_variant_current(uint32_t n, hd_syn_type syn_type, hd_variant_info *
         if (v[i].n == n && v[i].syn == (int)syn_type) ++c;
     info->index = c;
     return HD_OK;
+}
+
+hd_status hd_secded_variant_count(uint32_t n, hd_syn_type syn_type, uint32_t *count)
+{
+    if (!count) return HD_ERR_NULL;
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    uint32_t c = 0;
+    for (const auto &v : secded_variants())
+        if (v.n == n && v.syn == (int)syn_type) ++c;
+    *count = c;
+    return HD_OK;
+}
+
+hd_status hd_secded_variant_info_get(uint32_t n, hd_syn_type syn_type, uint32_t ordinal, hd_variant_info *info)
+{
+    if (!info) return HD_ERR_NULL;
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    uint32_t c = 0;
+    for (const StreamVariant &v : secded_variants()) {
+        if (v.n != n || v.syn != (int)syn_type) continue;
+        if (c++ != ordinal) continue;
+        std::memset(info, 0, sizeof(*info));
+        info->index = ordinal;
+        info->n = v.n;
+        info->syn_type = (uint32_t)v.syn;
+        info->codewords_per_thread = (uint32_t)v.G;
+        info->threads = (uint32_t)v.T;
+        info->stages = (uint32_t)v.S;
+        info->inplace = (uint32_t)v.inplace;
+        info->smem_bytes = v.smem;
+        info->chunk_codewords = v.chunk_cw;
+        info->blocks_per_sm = stream_blocks_per_sm(v.kernel, v.T, v.smem);
+        info->measured_us = -1.0f;
+        info->table_lookup = (uint32_t)v.lut;
+        return HD_OK;
+    }
+    return HD_ERR_INVALID_ARG;
+}
+
+hd_status hd_secded_variant_select(uint32_t n, hd_syn_type syn_type, int32_t ordinal)
+{
+    if (code_m(n) == 0) return HD_ERR_INVALID_N;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ordinal < 0) {
+        g_secded_choice.erase({dev, n, (int)syn_type});
+        return HD_OK;
+    }
+    int32_t c = 0;
+    const auto &v = secded_variants();
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (v[i].n == n && v[i].syn == (int)syn_type) {
+            if (c == ordinal) {
+                g_secded_choice[{dev, n, (int)syn_type}] = (int)i;
+                return HD_OK;
+            }
+            ++c;
+        }
+    }
+    return HD_ERR_INVALID_ARG;
 }
 
 hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, uint32_t reps, void *cuda_stream,

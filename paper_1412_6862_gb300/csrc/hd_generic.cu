@@ -98,7 +98,7 @@ int grid_for_tiles(uint64_t tiles)
 {
     const uint64_t want = (tiles + kGenericWarps - 1) / kGenericWarps;
     const uint64_t cap = (uint64_t)num_sms() * 8;
-    return (int)(want < cap ? want : cap);
+    return decode_grid(want, cap);
 }
 
 }  // namespace

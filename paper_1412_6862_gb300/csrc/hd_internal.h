@@ -27,6 +27,19 @@ inline uint64_t words_for_bits(uint64_t bits) { return (bits + 31) >> 5; }
 // Multiprocessor count of the current device (cached per device).
 int num_sms();
 
+// Upper bound on the CTAs of one decode launch (hd_set_max_ctas(); 0 = none).
+extern std::atomic<uint32_t> g_max_ctas;
+
+// Grid of a decode launch: `want` CTAs (enough for the work), at most `cap`
+// (what the device holds at once) and at most the caller's limit; at least 1.
+inline int decode_grid(uint64_t want, uint64_t cap)
+{
+    uint64_t g = want < cap ? want : cap;
+    const uint32_t lim = g_max_ctas.load(std::memory_order_relaxed);
+    if (lim != 0 && g > lim) g = lim;
+    return (int)(g > 0 ? g : 1);
+}
+
 // Generic warp-tile kernels (any supported n).  Warp tile t covers codewords
 // [32t, 32t+32); the launch covers warp tiles [tile_begin, tile_end).
 cudaError_t launch_decode_generic(const uint32_t *in, uint64_t in_words, uint32_t n, uint64_t num_cw,

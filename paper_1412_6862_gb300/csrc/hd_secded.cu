@@ -173,7 +173,7 @@ hd_status hd_decode_secded(const uint32_t *stream, uint64_t in_bits, uint32_t n,
     if (covered < num_codewords) {
         const uint64_t tiles = (num_codewords + 31) / 32 - covered / 32;
         const uint64_t want = (tiles + kTailWarps - 1) / kTailWarps, cap = (uint64_t)num_sms() * 8;
-        k_secded_tail<<<(int)std::min(want, cap), kTailWarps * 32, 0, st>>>(
+        k_secded_tail<<<decode_grid(want, cap), kTailWarps * 32, 0, st>>>(
             stream, words_for_bits(in_bits), n, (uint32_t)m, covered, num_codewords, out_bits,
             words_for_bits(num_codewords * k), syndromes, syn, err_count, detected_count);
         count_launch();

@@ -795,7 +795,7 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (a.ntiles + v.W - 1) / v.W;
-    const int grid = (int)std::min(want, cap);
+    const int grid = decode_grid(want, cap);
     v.launch[tsm](a, grid, smem, st);
     count_launch();
     return cudaGetLastError();
@@ -866,7 +866,7 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
     }
     const uint64_t tiles = (num_codewords + 31) / 32;
     const uint64_t want = (tiles + kSmallWarps - 1) / kSmallWarps, cap = (uint64_t)num_sms() * 8;
-    k_short_small<<<(int)std::min(want, cap), kSmallWarps * 32, 0, st>>>(
+    k_short_small<<<decode_grid(want, cap), kSmallWarps * 32, 0, st>>>(
         stream, words_for_bits(in_bits), n, r, num_codewords, out_bits, words_for_bits(num_codewords * k),
         syndromes, syn, err_count, detected_count);
     count_launch();

@@ -368,7 +368,7 @@ cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, ui
     if (bps <= 0) return cudaErrorInvalidConfiguration;
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
-    const int grid = (int)(want < cap ? want : cap);
+    const int grid = decode_grid(want, cap);
     kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
     count_launch();
     return cudaGetLastError();

@@ -135,6 +135,11 @@ SIGNATURES = {
     "hd_encode_secded": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_decode_host_batch": (_i32, [_c.POINTER(HostJob), _u32, _u64, _u32]),
     "hd_decode_host": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _c.POINTER(_c.c_ulonglong), _u64, _u32]),
+    "hd_secded_variant_count": (_i32, [_u32, _i32, _c.POINTER(_u32)]),
+    "hd_secded_variant_info_get": (_i32, [_u32, _i32, _u32, _VIP]),
+    "hd_secded_variant_select": (_i32, [_u32, _i32, _c.c_int32]),
+    "hd_set_max_ctas": (_i32, [_u32]),
+    "hd_get_max_ctas": (_u32, []),
     "hd_status_string": (_c.c_char_p, [_i32]),
     "hd_device_status": (_i32, [_c.POINTER(_u32)]),
     "hd_launch_count": (_u64, []),
@@ -258,6 +263,30 @@ def hd_variant_current(n: int, syn_type: int) -> dict:
     info = VariantInfo()
     check(lib().hd_variant_current(n, syn_type, ctypes.byref(info)), "hd_variant_current")
     return info.as_dict()
+
+
+def hd_secded_variant_count(n: int, syn_type: int) -> int:
+    c = _u32(0)
+    check(lib().hd_secded_variant_count(n, syn_type, ctypes.byref(c)), "hd_secded_variant_count")
+    return int(c.value)
+
+
+def hd_secded_variant_info_get(n: int, syn_type: int, ordinal: int) -> dict:
+    info = VariantInfo()
+    check(lib().hd_secded_variant_info_get(n, syn_type, ordinal, ctypes.byref(info)), "hd_secded_variant_info_get")
+    return info.as_dict()
+
+
+def hd_secded_variant_select(n: int, syn_type: int, ordinal: int) -> None:
+    check(lib().hd_secded_variant_select(n, syn_type, ordinal), "hd_secded_variant_select")
+
+
+def hd_set_max_ctas(max_ctas: int) -> None:
+    check(lib().hd_set_max_ctas(max_ctas), "hd_set_max_ctas")
+
+
+def hd_get_max_ctas() -> int:
+    return int(lib().hd_get_max_ctas())
 
 
 def hd_autotune(n: int, syn_type: int, num_codewords: int, reps: int = 5, cuda_stream=None) -> dict:

@@ -34,6 +34,28 @@ def expected(stream, n, N, syn_type, threads: int = 8):
     return out, syn, err
 
 
+def oracle_encode_parallel(encode, data: np.ndarray, n: int, N: int, k: int, L: int, threads: int = 0):
+    """The oracle encoder ``encode(data_words, n, count)`` over N codewords of
+    L bits (k data bits each), in host threads over ranges of whole 32-codeword
+    groups: every range starts on a word boundary of both the data and the
+    stream, so the ranges' words never overlap."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or (os.cpu_count() or 4)
+    per = max(32, ((N + threads - 1) // threads + 31) // 32 * 32)
+    out = np.zeros((N * L + 31) // 32, np.uint32)
+
+    def part(i0):
+        c = min(per, N - i0)
+        w = encode(data[i0 * k // 32:(i0 * k + c * k + 31) // 32], n, c)
+        o = i0 * L // 32
+        out[o:o + w.size] = w
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(part, range(0, N, per)))
+    return out
+
+
 def to_device(words: np.ndarray, pad_words: int = 0):
     import torch
     a = np.zeros(max(1, words.size + pad_words), np.uint32)

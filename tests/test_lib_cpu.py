@@ -201,3 +201,24 @@ def test_batch_tiles_host_only(lib):
     assert hd.lib().hd_batch_tiles(hd.packet_table([(16, 16, None, (1 << 40) + 1, 7, 0)]), 1, ctypes.byref(t)) == \
         hd.HD_ERR_SIZE
     assert hd.lib().hd_batch_tiles(None, 2, ctypes.byref(t)) == hd.HD_ERR_NULL
+
+
+def test_max_ctas_host_only(lib):
+    assert hd.hd_get_max_ctas() == 0
+    try:
+        hd.hd_set_max_ctas(3)
+        assert hd.hd_get_max_ctas() == 3
+    finally:
+        hd.hd_set_max_ctas(0)
+    assert hd.hd_get_max_ctas() == 0
+
+
+def test_secded_variants_host_only(lib):
+    for n in (7, 15, 31, 63, 127, 255):
+        for syn in (0, 1, 2):
+            if syn == 1 and n == 255:
+                continue
+            # the arithmetic configuration, plus the table one for n = 7 and 15
+            assert hd.hd_secded_variant_count(n, syn) == (2 if n in (7, 15) else 1)
+    assert hd.lib().hd_secded_variant_count(9, 0, None) in (hd.HD_ERR_NULL, hd.HD_ERR_INVALID_N)
+    assert hd.lib().hd_secded_variant_select(9, 0, 0) == hd.HD_ERR_INVALID_N

@@ -105,21 +105,23 @@ def test_secded_encoder_matches_oracle(n):
     assert np.array_equal(gc.host_u32(out)[:want.size], want)
 
 
-@pytest.mark.parametrize("n", [63, 255])
-def test_secded_full_size(n):
-    """2^24 (n = 63) or 2^22 (n = 255) codewords encoded on the GPU with
-    seeded channel errors: the counts match the injected events exactly
-    (every event gives a nonzero syndrome, exactly the doubles are detected)
-    and sampled codewords match the oracle."""
+# The SECDED benchmark workload at full size: 2^24 codewords for n <= 63, 2^22
+# above, p1 = 0.05 and p2 = 0.005 over the n + 1 bits, u16 syndromes.
+FULL_SECDED = [(7, 1 << 24), (15, 1 << 24), (31, 1 << 24), (63, 1 << 24), (127, 1 << 22), (255, 1 << 22)]
+
+
+@pytest.mark.parametrize("n,N", FULL_SECDED)
+def test_secded_full_size(n, N):
+    """Full-size streams in the launch configuration the benchmark times;
+    every data bit, every syndrome and both counts against the threaded
+    oracle, and the counts against the injected channel events (every event
+    gives a nonzero syndrome, exactly the doubles are detected).  Inputs:
+    the oracle encoder and the generator's errors."""
+    import os
     import torch
     m, k = hd.code_params(n)
-    N = (1 << 24) if n == 63 else (1 << 22)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(n)
-    data = torch.randint(-2**31, 2**31 - 1, (hd.words_for(N * k) + 4,), dtype=torch.int32, device="cuda",
-                         generator=gen)
-    enc = hd.encode_secded(data, n, N)
-    rx = gc.host_u32(enc).copy()
+    data = synth.random_words(n + 5, N * k)
+    rx = gc.oracle_encode_parallel(oracle.encode_secded, data, n, N, k, n + 1)
     ev = synth.error_events(n + 5, n + 1, N, p1=0.05, p2=0.005)
     synth.apply_errors(rx, ev)
     d_in = gc.to_device(rx, pad_words=4)
@@ -128,16 +130,12 @@ def test_secded_full_size(n):
     c = counts.cpu().numpy()
     assert int(c[0]) == ev.single_cw.size + ev.double_cw.size
     assert int(c[1]) == ev.double_cw.size
-    outh = gc.host_u32(out)
-    pick = np.unique(np.concatenate([synth.below(7, 3, 0, 2000, N), ev.double_cw[:300], [0, N - 1]]))
-    L = n + 1
-    sub_bits = np.concatenate([np.unpackbits(rx[(i * L) // 32:(i * L) // 32 + L // 32].view(np.uint8),
-                                             bitorder="little") for i in pick])
-    sub = np.packbits(sub_bits, bitorder="little").view(np.uint32)
-    eo, es, _, _ = oracle.decode_secded(sub, n, pick.size)
-    want = np.unpackbits(eo.view(np.uint8), bitorder="little")[:pick.size * k].reshape(-1, k)
-    allbits = np.unpackbits(outh.view(np.uint8), bitorder="little")
-    for j, i in enumerate(pick):
-        assert np.array_equal(allbits[int(i) * k:(int(i) + 1) * k], want[j]), f"codeword {i}"
-    assert np.array_equal(syn.cpu().numpy().view(np.uint16)[pick], es)
+    eo, es, ee, ed = oracle.decode_secded(rx, n, N, oracle.SYN_U16, threads=os.cpu_count() or 8)
+    nw = hd.words_for(N * k)
+    got = gc.host_u32(out)[:nw]
+    if not np.array_equal(got, eo[:nw]):
+        bad = np.nonzero(got != eo[:nw])[0]
+        raise AssertionError(f"n={n}: {bad.size} output words differ, first {bad[0]}")
+    assert np.array_equal(syn.cpu().numpy().view(np.uint16)[:N], es[:N])
+    assert (int(c[0]), int(c[1])) == (ee, ed)
     assert hd.hd_device_status() == 0

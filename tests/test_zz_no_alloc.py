@@ -1,13 +1,13 @@
 """hd_decode_batch_noalloc, the batched decode that allocates nothing, against
-the allocating entry point hd_decode_batch.
+the allocating entry point hd_decode_batch and against the CPU oracle.
 
 Some callers cannot allocate device memory: a process that budgets all device
 memory up front, an application whose allocator hooks forbid allocations from
 inside libraries, or a latency-critical receive path where an allocation could
 stall or fail.  For them the library keeps the batch tile table in a fixed 1 MiB
 device array.  These tests check that two calls in a row give bit-exactly the
-data bits, syndromes and error counts of hd_decode_batch, and that batches
-beyond the array's limits are refused.
+data bits, syndromes and error counts of hd_decode_batch and of the oracle,
+and that batches beyond the array's limits are refused.
 
 The file name sorts last, so a run that stops at the first failure has already
 run every other test.
@@ -15,6 +15,7 @@ run every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1412_6862_gb300 import hd, synth
 from tests import gpu_cases as gc
 
@@ -33,19 +34,22 @@ def _lib():
 
 def _packets(num, seed):
     """Mixed-n packets with mixed lengths and syndrome types, plus a second set
-    of output buffers for the reference decode."""
+    of output buffers for the reference decode, and the oracle's decode of
+    every packet."""
     import torch
     lengths = (3, 7, 15, 31, 63, 127, 255)
     ns = synth.below(seed, 21, 0, num, len(lengths))
     lens = synth.below(seed, 22, 0, num, 30000)
     stypes = synth.below(seed, 23, 0, num, 3)
-    mine, ref = [], []
+    mine, ref, want = [], [], []
     for j in range(num):
         n = lengths[int(ns[j])]
         N = 0 if j % 31 == 7 else int(lens[j])
         st = int(stypes[j])
         m, k = hd.code_params(n)
         stream, _, _ = gc.received_stream(n, N, seed=seed * 100 + j, p1=0.1, p2=0.02)
+        want.append(oracle.decode(stream, n, N, syn_type=st) if N else
+                    (np.zeros(0, np.uint32), np.zeros(0, np.uint8 if st == 1 else np.uint16) if st else None, 0))
         d_in = gc.to_device(stream)
         for dst in (mine, ref):
             out = torch.full((max(1, hd.words_for(N * k)),), -1, dtype=torch.int32, device="cuda")
@@ -53,7 +57,7 @@ def _packets(num, seed):
             if st != hd.SYN_NONE:
                 syn = torch.full((max(1, N),), 0x3C, dtype=torch.uint8 if st == 1 else torch.int16, device="cuda")
             dst.append((d_in, out, syn, N, n, st))
-    return mine, ref
+    return mine, ref, want
 
 
 def _table(pkts):
@@ -73,7 +77,7 @@ def _host(pkts, err):
 def test_noalloc_matches_allocating_batch_two_calls():
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    mine, ref = _packets(150, seed=3)
+    mine, ref, want = _packets(150, seed=3)
     num = len(mine)
     err_ref = torch.full((num,), 9, dtype=torch.int64, device="cuda")
     assert hd.hd_decode_batch(_table(ref), num, err_ref.data_ptr(), stream) == hd.HD_OK
@@ -93,10 +97,14 @@ def test_noalloc_matches_allocating_batch_two_calls():
         torch.cuda.synchronize()
         got, got_err = _host(mine, err)
         assert np.array_equal(got_err, expect_err), f"call {call}: error counts differ"
-        for j, ((go, gs), (eo, es)) in enumerate(zip(got, expect)):
+        for j, ((go, gs), (eo, es), (wo, ws, we)) in enumerate(zip(got, expect, want)):
             assert np.array_equal(go, eo), f"call {call}, packet {j}: data bits differ"
+            assert np.array_equal(go, wo), f"call {call}, packet {j}: data bits differ from the oracle"
+            assert got_err[j] == we, f"call {call}, packet {j}: error count differs from the oracle"
             if es is not None:
                 assert np.array_equal(gs, es), f"call {call}, packet {j}: syndromes differ"
+                gs_typed = gs.view(np.uint16) if gs.dtype != np.uint8 else gs
+                assert np.array_equal(gs_typed, ws), f"call {call}, packet {j}: syndromes differ from the oracle"
     assert hd.hd_device_status() == 0
 
 
