@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-packets", type=int, default=100000)
     ap.add_argument("--serve-rates", type=str, default="1e4,1e5,1e6", help="Poisson arrival rates, packets/s")
+    ap.add_argument("--serve-saturation-rates", type=str, default="2e6,4e6,8e6",
+                    help="higher rates tried in order until the server saturates")
+    ap.add_argument("--no-serve-host", action="store_true", help="skip serving from pinned host memory")
     ap.add_argument("--no-shortened", action="store_true", help="skip the shortened-code (M, t) grid section")
     ap.add_argument("--shortened-only", action="store_true", help="run only the shortened-code section")
     ap.add_argument("--short-steps", type=int, default=10, help="timed launches per (M, t) configuration")
@@ -73,6 +76,9 @@ def parse_args():
     ap.add_argument("--no-secded", action="store_true", help="skip the SECDED section")
     ap.add_argument("--secded-only", action="store_true", help="run only the SECDED section")
     ap.add_argument("--secded-codes", type=str, default="15,31,63,127,255")
+    ap.add_argument("--no-per-code", action="store_true", help="skip the per-code section (configs 1-3, p1 grid)")
+    ap.add_argument("--per-code-only", action="store_true", help="run only the per-code section")
+    ap.add_argument("--per-code-codes", type=str, default="", help="subset of the per-code section's codes")
     return ap.parse_args()
 
 
@@ -517,6 +523,118 @@ def run_shortened(dev, args, peak):
             "grid": rows, "setup_s": time.perf_counter() - t_setup}
 
 
+def l2_bytes(dev):
+    import torch
+    try:
+        return int(torch.cuda.get_device_properties(dev).L2_cache_size)
+    except Exception:
+        return 126 << 20
+
+
+def rotation_sets(footprint, dev, floor=2, cap=8):
+    """Buffer sets whose total is at least three times the L2, so that a launch
+    finds none of its inputs or outputs still in L2 from the launch before."""
+    need = (3 * l2_bytes(dev) + footprint - 1) // max(1, footprint)
+    return int(max(floor, min(cap, need)))
+
+
+def time_graph(dev, calls, rounds, warm=2):
+    """Capture `calls` (one launch each) `rounds` times over in one CUDA graph,
+    replay it `warm` times untimed and once timed with CUDA events on the
+    stream it runs on; returns seconds per call."""
+    import torch
+    stream = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        for c in calls:  # warm-up outside the capture (first-use set-up of the library)
+            c(stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(rounds):
+                for c in calls:
+                    c(stream.cuda_stream)
+        for _ in range(warm):
+            g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    del g
+    return a.elapsed_time(b) / 1e3 / (rounds * len(calls))
+
+
+# Every benchmark configuration of a single code (the codes and error rates the
+# workload names): (label, n, codewords, [(p1, p2)], syndrome bytes).
+PER_CODE = (
+    ("Hamming(7,4), 2^20 codewords, p1=0.1, u8 syndromes", 7, 1 << 20, ((0.1, 0.0),), 1),
+    ("Hamming(15,11), 2^24 codewords, u8 syndromes", 15, 1 << 24, ((0.01, 0.01), (0.1, 0.01), (0.5, 0.01)), 1),
+    ("Hamming(31,26), 2^24 codewords, u8 syndromes", 31, 1 << 24, ((0.01, 0.01), (0.1, 0.01), (0.5, 0.01)), 1),
+    ("Hamming(63,57), 2^24 codewords, u8 syndromes", 63, 1 << 24, ((0.01, 0.01), (0.1, 0.01), (0.5, 0.01)), 1),
+    ("Hamming(127,120), 2^22 codewords, p1=0.05, p2=0.005, u16 syndromes", 127, 1 << 22, ((0.05, 0.005),), 2),
+    ("Hamming(255,247), 2^22 codewords, p1=0.05, p2=0.005, u16 syndromes", 255, 1 << 22, ((0.05, 0.005),), 2),
+)
+
+
+def run_per_code(dev, args, peak):
+    """Each code of the workload alone, at every error rate it names: hd_decode
+    launches replayed from a CUDA graph over rotating buffer sets (three times
+    the L2 in total, so every launch streams from HBM), except (7,4) at 2^20
+    codewords, whose 2.5 MB stay in L2 by design and which is reported per
+    launch.  The error count is checked against the injected events (every
+    event of weight 1 or 2 gives a nonzero syndrome)."""
+    import torch
+    from paper_1412_6862_gb300 import hd, synth
+    res = []
+    codes = {int(c) for c in args.per_code_codes.split(",")} if args.per_code_codes else None
+    for label, n, N, rates, sb in PER_CODE:
+        if codes is not None and n not in codes:
+            continue
+        m, k = code_params(n)
+        syn_t = hd.SYN_U8 if sb == 1 else hd.SYN_U16
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2000 + n)
+        data = torch.randint(-2**31, 2**31 - 1, (hd.words_for(N * k) + 4,), dtype=torch.int32, device=dev,
+                             generator=gen)
+        clean = hd.encode(data, n, N).cpu().numpy().view(np.uint32).copy()
+        del data
+        nbytes = algorithmic_bytes(n, N, sb)
+        l2_resident = N * n // 8 < l2_bytes(dev) // 16
+        for p1, p2 in rates:
+            host = clean.copy()
+            ev = synth.error_events(3000 + n, n, N, p1=p1, p2=p2)
+            synth.apply_errors(host, ev)
+            d0 = torch.from_numpy(host.view(np.int32)).to(dev)
+            nsets = 1 if l2_resident else rotation_sets(nbytes, dev)
+            sets = []
+            for i in range(nsets):
+                d_in = d0 if i == 0 else d0.clone()
+                out = torch.empty(hd.words_for(N * k) + 4, dtype=torch.int32, device=dev)
+                syn = torch.empty(N * sb + 16, dtype=torch.uint8, device=dev)
+                err = torch.empty(1, dtype=torch.int64, device=dev)
+                sets.append((d_in, out, syn, err))
+
+            def call(bset):
+                d_in, out, syn, err = bset
+                return lambda sh: hd.check(hd.hd_decode(d_in.data_ptr(), N * n, n, N, out.data_ptr(),
+                                                        syn.data_ptr(), syn_t, err.data_ptr(), sh), "hd_decode")
+
+            rounds = 100 if l2_resident else max(2, 12 // nsets)
+            t = time_graph(dev, [call(b) for b in sets], rounds)
+            errs = [int(b[3].item()) for b in sets]
+            res.append({"config": label, "n": n, "codewords": N, "p1": p1, "p2": p2,
+                        "us_per_launch": t * 1e6, "gbps": N * k / t / 1e9, "hbm_frac": nbytes / t / 1e9 / peak,
+                        "algorithmic_bytes": nbytes, "buffer_sets": nsets, "l2_resident": bool(l2_resident),
+                        "err_count": errs[0], "injected_events": int(ev.num_events),
+                        "err_count_matches_events": all(e == ev.num_events for e in errs)})
+            del sets, d0, host
+            torch.cuda.empty_cache()
+    return {"workload": "each code alone at every error rate the configurations name; hd_decode replayed from a "
+                        "CUDA graph over rotating buffer sets (>= 3x L2 in total) except the L2-resident (7,4) "
+                        "stream, whose per-launch time is reported as such", "rows": res}
+
+
 SECDED_P1, SECDED_P2 = 0.05, 0.005
 
 
@@ -583,37 +701,83 @@ def run_secded(dev, args, peak):
                         f"u16 syndromes; one hd_decode_secded / hd_decode launch each", "codes": res}
 
 
-def run_serving(dev, args, pool=None):
-    """Open-loop Poisson arrivals of packets from the batched distribution
-    (payloads pre-staged in device memory), served with continuous batching
-    under a 4 GB admission budget: p50/p99 latency and sustained Gbit/s."""
+def serve_rates(args):
+    """The named rates, then doubling rates until the server saturates."""
+    base = [float(r) for r in args.serve_rates.split(",")]
+    extra = [float(r) for r in args.serve_saturation_rates.split(",")] if args.serve_saturation_rates else []
+    return base, extra
+
+
+def run_serving(dev, args, pool=None, host=False):
+    """Open-loop Poisson arrivals of packets from the batched distribution,
+    served with continuous batching under a 4 GB admission budget: p50/p99
+    latency and sustained Gbit/s per arrival rate, then higher rates until the
+    sustained rate falls below 90 % of the offered one or arrivals have to
+    wait for queue room (saturation).  host=False: payloads pre-staged in
+    device memory, arrival = descriptor enqueue.  host=True: payloads and
+    results in pinned host memory (hd_serve_trace_host), so the latency
+    includes the gather and scatter copies; per-wave stage times (T_PS, T_DKE,
+    T_PR) are reported beside Eq. 1 and its slowest-stage form."""
+    import torch
     from paper_1412_6862_gb300 import hd, synth
     t_setup = time.perf_counter()
     layout, d_in, d_out, d_syn = pool if pool is not None else build_batched(dev, args.batched_packets)
     P = len(layout)
-    bi, bo, bs = d_in.data_ptr(), d_out.data_ptr(), d_syn.data_ptr()
+    if host:
+        h_in = d_in.cpu().pin_memory()
+        h_out = torch.empty(d_out.numel(), dtype=torch.int32).pin_memory()
+        h_syn = torch.empty(d_syn.numel(), dtype=torch.uint8).pin_memory()
+        bi, bo, bs = h_in.data_ptr(), h_out.data_ptr(), h_syn.data_ptr()
+    else:
+        bi, bo, bs = d_in.data_ptr(), d_out.data_ptr(), d_syn.data_ptr()
     rows = [(bi + 4 * oi, bo + 4 * oo, bs + osy, N, n, hd.SYN_U8) for (n, N, oi, oo, osy, od, iw, ow, dw) in layout]
     bits = [N * code_params(n)[1] for (n, N, *_r) in layout]
     num = args.serve_packets
     table = hd.packet_table([rows[j % P] for j in range(num)])
+    staging = (256 << 20) if host else 0
     cfg = hd.server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=1 << 16,
-                           queue_capacity=max(1 << 16, num), mem_cap_bytes=4 << 30)
+                           queue_capacity=max(1 << 16, num), mem_cap_bytes=4 << 30, host_staging_bytes=staging)
     setup_s = time.perf_counter() - t_setup
-    out = {"workload": f"open-loop Poisson arrivals of packets from the batched distribution ({P}-packet device "
-                       f"pool, cycled), {num} packets per rate; continuous batching with 4 wave slots, <= 4096 "
+    src = "pinned host memory (gather, decode and scatter per wave on the slot's stream)" if host else \
+        "a device pool (arrival = descriptor enqueue)"
+    out = {"workload": f"open-loop Poisson arrivals of packets from the batched distribution ({P}-packet pool in "
+                       f"{src}, cycled), {num} packets per rate; continuous batching with 4 wave slots, <= 4096 "
                        f"packets per wave, 4 GB admission budget; latency = scheduled arrival -> completion seen "
                        f"by the host", "setup_s": setup_s, "rates": {}}
-    for rate in (float(r) for r in args.serve_rates.split(",")):
+    base, extra = serve_rates(args)
+    best, saturated_at = 0.0, None
+    for i, rate in enumerate(base + extra):
+        if i >= len(base) and saturated_at is not None:
+            break
         arr = synth.poisson_arrivals(int(rate) % 1000003, num, rate)
-        comps, st = hd.hd_serve_trace(cfg, table, arr, num)
+        comps, st = hd.hd_serve_trace(cfg, table, arr, num, host=host)
+        bad = sum(1 for j in range(num) if comps[j].status != hd.HD_OK)
         decoded = sum(bits[j % P] for j in range(num))
-        out["rates"][f"{rate:g}"] = {
-            "p50_latency_us": st["p50_latency_us"], "p99_latency_us": st["p99_latency_us"],
-            "max_latency_us": st["max_latency_us"],
-            "sustained_gbps": decoded / st["duration_s"] / 1e9 if st["duration_s"] > 0 else None,
-            "offered_gbps": decoded / float(arr[-1]) / 1e9, "duration_s": st["duration_s"],
-            "waves": st["waves"], "mean_wave_packets": st["mean_wave_packets"],
-            "max_resident_gb": st["max_resident_bytes"] / 1e9, "backpressure_waits": st["backpressure_waits"]}
+        sustained = decoded / st["duration_s"] / 1e9 if st["duration_s"] > 0 else None
+        offered = decoded / float(arr[-1]) / 1e9
+        row = {"p50_latency_us": st["p50_latency_us"], "p99_latency_us": st["p99_latency_us"],
+               "max_latency_us": st["max_latency_us"], "sustained_gbps": sustained, "offered_gbps": offered,
+               "duration_s": st["duration_s"], "waves": st["waves"], "mean_wave_packets": st["mean_wave_packets"],
+               "max_resident_gb": st["max_resident_bytes"] / 1e9, "backpressure_waits": st["backpressure_waits"],
+               "failed_packets": bad}
+        if host and st["host_waves"]:
+            tp, tk, tr = st["mean_t_in_us"] * 1e-6, st["mean_t_decode_us"] * 1e-6, st["mean_t_out_us"] * 1e-6
+            w = st["host_waves"]
+            row.update({"t_ps_us": tp * 1e6, "t_dke_us": tk * 1e6, "t_pr_us": tr * 1e6,
+                        "eq1_prediction": eq1_speedup(w, tp, tk, tr),
+                        "slowest_stage_prediction": pipeline_speedup(w, tp, tk, tr),
+                        "overlap": w * (tp + tk + tr) / st["duration_s"] if st["duration_s"] > 0 else None})
+        out["rates"][f"{rate:g}"] = row
+        if sustained:
+            best = max(best, sustained)
+        if saturated_at is None and (st["backpressure_waits"] > 0 or (sustained or 0) < 0.9 * offered):
+            saturated_at = rate
+    out["saturation"] = {"max_sustained_gbps": best, "saturated_at_rate": saturated_at,
+                         "rule": "the first rate whose sustained Gbit/s fell below 90 % of the offered load or "
+                                 "whose arrivals waited for queue room"}
+    if host and "rates" in out:
+        out["note"] = ("overlap = waves x (T_PS + T_DKE + T_PR) / duration: the mean number of wave stages in "
+                       "flight at once, the achieved counterpart of the two predictions")
     return out
 
 
@@ -731,8 +895,9 @@ def run_ours(args):
         return
     if args.serve_only:
         res = run_serving(dev, args)
+        res_h = None if args.no_serve_host else run_serving(dev, args, host=True)
         if rank == 0:
-            print(json.dumps({"serving": res}), flush=True)
+            print(json.dumps({"serving": res, "serving_host": res_h}), flush=True)
         return
     if args.secded_only:
         res = run_secded(dev, args, peaks()[0])
@@ -743,6 +908,11 @@ def run_ours(args):
         res = run_shortened(dev, args, peaks()[0])
         if rank == 0:
             print(json.dumps({"shortened": res}), flush=True)
+        return
+    if args.per_code_only:
+        res = run_per_code(dev, args, peaks()[0])
+        if rank == 0:
+            print(json.dumps({"per_code": res}), flush=True)
         return
 
     codes = tuple(int(c) for c in args.codes.split(","))
@@ -859,6 +1029,27 @@ def run_ours(args):
     traffic = recorded_traffic(kernel_desc) if roof_n == ROOFLINE_N else None
     achieved = roof_bytes / (kern_ms / 1e3) / 1e9
     clocks = clk.summary()
+    # the whole step against the same peak: every byte the step's launches
+    # move over the step's time, so no output written back after a kernel's
+    # end event escapes the count
+    step_bytes = sum(algorithmic_bytes(n, SWEEP_N) for n in codes)
+    step_frac = step_bytes / (ms / args.steps / 1e3) / 1e9 / peak
+    # the roofline kernel back to back: ten launches in one graph over two
+    # buffer sets, so each launch also pays for its predecessor's write-back
+    b = bufs[roof_n]
+    spare = dict(d_in=b["d_in"].clone(), out=torch.empty_like(b["out"]), syn=torch.empty_like(b["syn"]),
+                 err=torch.empty_like(b["err"]))
+
+    def roof_call(bs):
+        return lambda sh_: hd.check(hd.hd_decode(bs["d_in"].data_ptr(), roof_n * SWEEP_N, roof_n, SWEEP_N,
+                                                 bs["out"].data_ptr(), bs["syn"].data_ptr(), hd.SYN_U8,
+                                                 bs["err"].data_ptr(), sh_), "hd_decode")
+
+    t_b2b = time_graph(dev, [roof_call(b), roof_call(spare)], 5)
+    del spare
+    torch.cuda.empty_cache()
+    b2b = {"launches": 10, "us_per_launch": t_b2b * 1e6, "achieved": roof_bytes / t_b2b / 1e9,
+           "frac": roof_bytes / t_b2b / 1e9 / peak}
 
     # end to end through the C ABI with HOST buffers: hd_decode_host copies each
     # stream from pinned host memory, decodes it and copies data bits,
@@ -897,8 +1088,11 @@ def run_ours(args):
     pool = None
     if not args.no_batched:
         batched, pool = run_batched(dev, args, peak, keep_pool=True)
+    serving_host = None
     if not args.no_serve:
         serving = run_serving(dev, args, pool)
+        if not args.no_serve_host:
+            serving_host = run_serving(dev, args, pool, host=True)
     pool = None
     shortened = None
     if not args.no_shortened:
@@ -908,6 +1102,10 @@ def run_ours(args):
     if not args.no_secded:
         torch.cuda.empty_cache()
         secded = run_secded(dev, args, peak)
+    per_code = None
+    if not args.no_per_code:
+        torch.cuda.empty_cache()
+        per_code = run_per_code(dev, args, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -926,15 +1124,22 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"hd_decode n={roof_n}, N=2^24 ({roof_bytes} algorithmic bytes/launch, "
-                                   f"{kern_ms * 1e3:.2f} us avg; {kernel_desc})", "peak_kind": peak_kind},
+                                   f"{kern_ms * 1e3:.2f} us avg; {kernel_desc})", "peak_kind": peak_kind,
+                         "step_frac": step_frac, "step_bytes": step_bytes, "back_to_back": b2b,
+                         "note": "frac times the kernel between events on its stream, and up to a fifth of its "
+                                 "output can still be in L2 at its end event (traffic < algorithmic bytes); "
+                                 "step_frac (the whole step's bytes over the step's time) and back_to_back (ten "
+                                 "launches in one graph, each paying for the previous write-back) include it"},
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,
+            "serving_host": serving_host,
             "shortened": shortened,
             "secded": secded,
+            "per_code": per_code,
             "adt": adt,
         }
         print(json.dumps(line), flush=True)

@@ -395,34 +395,44 @@ hd_status hd_batch_tiles(const hd_packet *table, uint32_t num_packets, uint64_t 
  * Serving: continuous batching of arriving packets.
  *
  * A server owns a scheduler thread and `max_waves` wave slots (one CUDA
- * stream each).  Packets already resident in device memory are submitted from
- * any thread; whenever a slot is free the scheduler admits waiting packets in
- * arrival order, as many as the slot's limits and the device-memory budget
- * (in + out + syndrome bytes of admitted, unfinished packets <= mem_cap_bytes)
- * allow, and launches them as one batched decode on that slot's stream.  Waves
- * on different slots overlap on the GPU, so packets arriving while others are
- * being decoded start as soon as a slot and budget free up.  This applies the
- * paper's asynchronous pipelining of successive packets (Sec. III-B) to
- * device-resident packets.  Results are exactly those of hd_decode() on each
- * packet alone.
+ * stream each).  Packets are submitted from any thread, either resident in
+ * device memory (hd_server_submit) or in pinned host memory
+ * (hd_server_submit_host); whenever a slot is free the scheduler admits
+ * waiting packets in arrival order, as many as the slot's limits and the
+ * device-memory budget (in + out + syndrome bytes of admitted, unfinished
+ * packets <= mem_cap_bytes) allow, and launches them as one batched decode on
+ * that slot's stream.  A wave that carries host packets first gathers their
+ * input into the slot's device staging (one copy kernel reading the pinned
+ * buffers), and after the decode scatters data bits and syndromes back into
+ * the caller's host buffers (a second copy kernel), all on the slot's stream.
+ * Waves on different slots overlap on the GPU, so packets arriving while
+ * others are being copied or decoded start as soon as a slot and budget free
+ * up: the paper's asynchronous pipelining of successive packets (Sec. III-B,
+ * Fig. 5, Eq. 1).  Results are exactly those of hd_decode() on each packet
+ * alone.
  * ------------------------------------------------------------------------- */
 typedef struct hd_server hd_server;
 
 typedef struct {
-    uint32_t max_waves;        /* wave slots (concurrent batched launches), 1..64 */
-    uint32_t max_wave_packets; /* packets per wave */
-    uint32_t max_wave_tiles;   /* tile-table capacity per wave (a packet of N codewords needs <= N/128 + 1) */
-    uint32_t queue_capacity;   /* submitted packets waiting for admission */
-    uint64_t mem_cap_bytes;    /* admission budget in bytes (see above) */
+    uint32_t max_waves;          /* wave slots (concurrent batched launches), 1..64 */
+    uint32_t max_wave_packets;   /* packets per wave */
+    uint32_t max_wave_tiles;     /* tile-table capacity per wave (a packet of N codewords needs <= N/128 + 1) */
+    uint32_t queue_capacity;     /* submitted packets waiting for admission */
+    uint64_t mem_cap_bytes;      /* admission budget in bytes (see above) */
+    uint64_t host_staging_bytes; /* device staging per slot for host packets (0: hd_server_submit_host is refused);
+                                    a host packet takes its input, output and syndrome sizes, each rounded up
+                                    to 16 bytes */
 } hd_server_config;
 
 typedef struct {
     uint64_t tag;         /* the caller's tag from hd_server_submit */
-    uint64_t err_count;   /* nonzero syndromes in the packet */
-    uint64_t t_submit_ns; /* steady-clock times: submitted, admitted into a wave, completion seen */
+    uint64_t err_count;   /* nonzero syndromes in the packet (0 unless status is HD_OK or HD_ERR_TIMEOUT) */
+    uint64_t t_submit_ns; /* steady-clock times: submitted, admitted into a wave (0 if never), completion seen */
     uint64_t t_admit_ns;
     uint64_t t_done_ns;
-    int32_t status;       /* HD_OK, or HD_ERR_CUDA if the wave failed */
+    int32_t status;       /* HD_OK; HD_ERR_TIMEOUT if a bounded wait of its wave's kernel ran out (the
+                             outputs are then not to be trusted); HD_ERR_CUDA if its wave failed or the
+                             server had failed before admitting it */
 } hd_completion;
 
 typedef struct {
@@ -430,29 +440,53 @@ typedef struct {
     uint64_t waves;                          /* batched launches */
     uint64_t max_resident_bytes;             /* high-water mark of the admission budget */
     double mean_wave_packets;
-    /* filled by hd_serve_trace: latency from scheduled arrival to completion */
+    /* filled by hd_serve_trace / hd_serve_trace_host: latency from scheduled arrival to completion */
     double p50_latency_us, p99_latency_us, max_latency_us;
     double duration_s;           /* first arrival to last completion */
     uint64_t backpressure_waits; /* submissions retried because the queue was full */
+    /* waves that carried host packets, and their mean stage times measured by CUDA events on the
+       slot's stream: gather (T_PS), batched decode (T_DKE), scatter (T_PR) */
+    uint64_t host_waves;
+    double mean_t_in_us, mean_t_decode_us, mean_t_out_us;
 } hd_server_stats;
 
 /* Create a server on the current device (allocates its slots: per slot a
- * stream, an event, a device tile table and pinned staging). */
+ * stream, events, device tile and copy tables, host_staging_bytes of device
+ * staging and pinned host staging) and performs the batch kernel's one-time
+ * set-up, so that the first wave pays none of it. */
 hd_status hd_server_create(const hd_server_config *cfg, hd_server **server);
 
 /* Queue one packet (device buffers as in hd_packet; they must stay valid until
  * its completion is polled).  Thread-safe.  HD_ERR_CAPACITY when the queue is
- * full or the packet alone exceeds the budget or a wave's tile capacity. */
+ * full or the packet alone exceeds the budget or a wave's tile capacity; the
+ * server's error once it has failed. */
 hd_status hd_server_submit(hd_server *server, const hd_packet *packet, uint64_t tag);
+
+/* Queue one packet whose in, out and syndromes buffers are pinned HOST memory
+ * (cudaMallocHost, cudaHostAlloc or cudaHostRegister; 16-byte aligned; sizes
+ * as in hd_packet).  The input is read and the results written by the
+ * packet's wave; the buffers must stay valid until its completion is polled.
+ * HD_ERR_INVALID_ARG when the server has no host staging or a buffer is not
+ * pinned host memory that kernels can reach; HD_ERR_CAPACITY as
+ * hd_server_submit, or when the packet alone exceeds host_staging_bytes. */
+hd_status hd_server_submit_host(hd_server *server, const hd_packet *packet, uint64_t tag);
 
 /* Move up to `max` completions (in completion order) to `out`; *count gets the
  * number moved.  Returns the server's sticky error, if any. */
 hd_status hd_server_poll(hd_server *server, hd_completion *out, uint32_t max, uint32_t *count);
 
-/* Wait until every submitted packet has completed (HD_ERR_TIMEOUT after timeout_ns). */
+/* Wait until every submitted packet has completed (HD_ERR_TIMEOUT after
+ * timeout_ns; the server's error at once if it has failed). */
 hd_status hd_server_drain(hd_server *server, uint64_t timeout_ns);
 
 hd_status hd_server_get_stats(hd_server *server, hd_server_stats *stats);
+
+/* Failure injection for tests, on the host: the server's next `count` wave
+ * launches fail as a CUDA launch error would, before anything of those waves
+ * is enqueued.  A failed wave completes its packets with HD_ERR_CUDA, the
+ * server keeps HD_ERR_CUDA as its error, admits nothing more and completes
+ * every waiting packet with that error.  No GPU work fails. */
+hd_status hd_server_inject_launch_failures(hd_server *server, uint32_t count);
 
 /* Finish the admitted and queued packets, stop the scheduler and free the slots. */
 void hd_server_destroy(hd_server *server);
@@ -463,6 +497,11 @@ void hd_server_destroy(hd_server *server);
  * p50/p99 latency from scheduled arrival to observed completion. */
 hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *packets, const double *arrival_s,
                          uint32_t num, hd_completion *completions, hd_server_stats *stats);
+
+/* hd_serve_trace with every packet submitted from pinned host memory
+ * (hd_server_submit_host): the latency includes the copies in and out. */
+hd_status hd_serve_trace_host(const hd_server_config *cfg, const hd_packet *packets, const double *arrival_s,
+                              uint32_t num, hd_completion *completions, hd_server_stats *stats);
 
 /* Human-readable name of a status code (static storage). */
 const char *hd_status_string(hd_status status);

@@ -597,7 +597,7 @@ hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::ve
 }
 
 cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32_t *d_counter,
-                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st)
+                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st, uint32_t *status)
 {
     hd_plan p;
     p.num_packets = num_packets;
@@ -606,6 +606,7 @@ cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32
     p.d_counter = d_counter;
     LaunchGeom geom;
     cudaError_t e = prepare_plan(&p, &geom, st);
+    if (status != nullptr) geom.status = status;
     if (e == cudaSuccess) e = enqueue_plan(&p, geom, d_err, st);
     if (e == cudaSuccess && num_tiles) count_launch();
     return e;

@@ -62,8 +62,41 @@ hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::ve
 // Enqueue one batched decode of a device tile table on `st`: clear the claim
 // counter and the error counters (when err is not NULL), then launch the batch
 // kernel in its default configuration.  Host-side setup (kernel attributes,
-// occupancy, status word) happens on the first call per device.
+// occupancy, status word) happens on the first call per device.  A timeout
+// is latched into `status` (device) when not NULL, else into the device's
+// status word.  num_tiles = 0 performs only the set-up and the clears.
 cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32_t *d_counter,
-                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st);
+                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st,
+                              uint32_t *status = nullptr);
+
+// A contiguous copy of at most kPieceBytes between two 16-byte aligned
+// addresses that kernels can dereference (device memory, or pinned host memory
+// through its device-accessible address).
+struct CopyPiece {
+    const void *src;
+    void *dst;
+    uint32_t bytes;
+    uint32_t pad;
+};
+
+constexpr uint32_t kPieceBytes = 32768;
+
+// Cut a copy of `bytes` into pieces appended to `out`.
+inline void add_copy_pieces(std::vector<CopyPiece> &out, const void *src, void *dst, uint64_t bytes)
+{
+    for (uint64_t o = 0; o < bytes; o += kPieceBytes) {
+        CopyPiece p;
+        p.src = static_cast<const unsigned char *>(src) + o;
+        p.dst = static_cast<unsigned char *>(dst) + o;
+        p.bytes = (uint32_t)((bytes - o) < kPieceBytes ? (bytes - o) : kPieceBytes);
+        p.pad = 0;
+        out.push_back(p);
+    }
+}
+
+// Copy every piece of a device table of `count` pieces (one CTA per piece,
+// 16-byte vector loads and stores; the last bytes of a piece that is not a
+// multiple of 16 are copied one by one, so nothing past `bytes` is touched).
+cudaError_t launch_copy_pieces(const CopyPiece *d_pieces, uint32_t count, cudaStream_t st);
 
 }  // namespace hd

@@ -8,12 +8,19 @@
 // slot's stream.  Waves on different slots run concurrently on the GPU, so
 // packets that arrive while others are being decoded join the next free slot
 // instead of waiting for the whole device to drain.  Completion is detected by
-// polling the slot's event; the packet's error count comes back through a
-// pinned host buffer copied on the same stream.
+// polling the slot's event; the packets' error counts and the wave's own
+// device status word come back through a pinned host buffer copied on the
+// same stream.
 //
-// This applies the paper's asynchronous pipelining idea (Sec. III-B: overlap
-// the independent work of successive packets) to packets that are already in
-// device memory: the overlap is between waves of decodes.
+// Packets can also be submitted from pinned host memory (an SDR receive path
+// gets its packets there).  A wave that carries such packets gathers them into
+// the slot's device staging with one copy kernel (T_PS), decodes (T_DKE) and
+// scatters data bits and syndromes back into the caller's host buffers with a
+// second copy kernel (T_PR), all on the slot's stream; events between the
+// stages time them.  Waves on different slots overlap, so one wave's
+// transfers run beside another's decode: the paper's asynchronous data
+// transfer (Sec. III-B, Fig. 5, Eq. 1) applied to a stream of arriving
+// packets.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -59,25 +66,42 @@ bool packet_cost(const hd_packet &q, uint64_t *bytes, uint64_t *tiles, hd_status
 }
 
 struct Req {
-    hd_packet pkt;
+    hd_packet pkt;   // as submitted (host pointers for a host packet)
     uint64_t tag;
     uint64_t t_submit;
-    uint64_t bytes;
+    uint64_t bytes;  // algorithmic bytes (input + output + syndromes)
     uint64_t tiles;
+    bool host = false;
+    // host packets: device-accessible addresses of the caller's pinned buffers,
+    // their exact sizes, and the staging they take (each part 16-byte rounded)
+    const void *dev_in = nullptr;
+    void *dev_out = nullptr, *dev_syn = nullptr;
+    uint64_t in_b = 0, out_b = 0, syn_b = 0, stage_b = 0;
 };
+
+inline uint64_t round16(uint64_t b) { return (b + 15) & ~15ull; }
 
 struct Wave {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;                // completion
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // stage timing of host waves: before and after the gather,
+    cudaEvent_t t2 = nullptr, t3 = nullptr;  // after the decode and after the scatter
+    char *dmem = nullptr;                    // one allocation: tiles, pieces, counter, status + counts, staging
     DevTile *d_tiles = nullptr;
+    CopyPiece *d_pieces = nullptr;
     uint32_t *d_counter = nullptr;
+    uint32_t *d_status = nullptr;            // the wave's status word, followed by the error counts
     unsigned long long *d_err = nullptr;
-    DevTile *h_tiles = nullptr;            // pinned staging of the tile table
-    unsigned long long *h_err = nullptr;   // pinned copy of the error counts
+    unsigned char *d_stage = nullptr;
+    DevTile *h_tiles = nullptr;              // pinned staging of the tile table
+    CopyPiece *h_pieces = nullptr;           // pinned staging of the copy pieces
+    uint32_t *h_back = nullptr;              // pinned: status word (16 bytes), then the error counts
     std::vector<Req> reqs;
     uint64_t bytes = 0;
+    uint64_t stage_used = 0;
     uint64_t t_admit = 0;
     bool busy = false;
+    bool host = false;                       // carries host packets (timed stages)
 };
 
 }  // namespace
@@ -99,7 +123,10 @@ struct hd_server {
     std::thread worker;
     std::atomic<bool> stop{false};
     std::atomic<int> busy_waves{0};
+    std::atomic<uint32_t> inject_failures{0};  // test hook: wave launches to fail on the host
     hd_status error = HD_OK;
+    uint64_t pieces_cap = 0;                    // copy pieces per wave
+    double t_in_us = 0, t_dec_us = 0, t_out_us = 0;  // summed stage times of host waves
 };
 
 namespace {
@@ -108,11 +135,13 @@ void release_waves(hd_server *s)
 {
     for (Wave &w : s->waves) {
         if (w.st) cudaStreamSynchronize(w.st);
-        if (w.ev) cudaEventDestroy(w.ev);
+        for (cudaEvent_t e : {w.ev, w.t0, w.t1, w.t2, w.t3})
+            if (e) cudaEventDestroy(e);
         if (w.st) cudaStreamDestroy(w.st);
-        if (w.d_tiles) cudaFree(w.d_tiles);
+        if (w.dmem) cudaFree(w.dmem);
         if (w.h_tiles) cudaFreeHost(w.h_tiles);
-        if (w.h_err) cudaFreeHost(w.h_err);
+        if (w.h_pieces) cudaFreeHost(w.h_pieces);
+        if (w.h_back) cudaFreeHost(w.h_back);
         w = Wave();
     }
 }
@@ -120,29 +149,126 @@ void release_waves(hd_server *s)
 // Launch one wave from the requests in w.reqs; false on a CUDA failure.
 bool launch_wave(hd_server *s, Wave &w)
 {
+    // test hook: fail as a launch error would, before anything is enqueued
+    for (uint32_t f = s->inject_failures.load(); f > 0;)
+        if (s->inject_failures.compare_exchange_weak(f, f - 1)) return false;
+    // the batch table: device packets as submitted, host packets pointed at
+    // their part of the slot's staging; copy pieces for the host packets
     std::vector<hd_packet> table;
     table.reserve(w.reqs.size());
-    for (const Req &r : w.reqs) table.push_back(r.pkt);
+    std::vector<CopyPiece> gin, gout;
+    uint64_t off = 0;
+    for (const Req &r : w.reqs) {
+        hd_packet q = r.pkt;
+        if (r.host) {
+            unsigned char *din = w.d_stage + off;
+            unsigned char *dout = din + round16(r.in_b);
+            unsigned char *dsyn = dout + round16(r.out_b);
+            off += r.stage_b;
+            add_copy_pieces(gin, r.dev_in, din, r.in_b);
+            add_copy_pieces(gout, dout, r.dev_out, r.out_b);
+            if (r.syn_b) add_copy_pieces(gout, dsyn, r.dev_syn, r.syn_b);
+            q.in = reinterpret_cast<const uint32_t *>(din);
+            q.out = reinterpret_cast<uint32_t *>(dout);
+            q.syndromes = r.syn_b ? dsyn : nullptr;
+            if (!r.syn_b) q.syn_type = HD_SYN_NONE;
+        }
+        table.push_back(q);
+    }
     std::vector<DevTile> tiles;
     if (build_tile_table(table.data(), (uint32_t)table.size(), tiles, nullptr) != HD_OK) return false;
     if (tiles.size() > s->cfg.max_wave_tiles) return false;  // admission bounds the tiles; never reached
-    if (!tiles.empty()) std::memcpy(w.h_tiles, tiles.data(), tiles.size() * sizeof(DevTile));
-    if (!tiles.empty() &&
-        cudaMemcpyAsync(w.d_tiles, w.h_tiles, tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice, w.st) !=
+    if (gin.size() + gout.size() > s->pieces_cap) return false;  // bounded by the staging; never reached
+    if (!tiles.empty()) {
+        std::memcpy(w.h_tiles, tiles.data(), tiles.size() * sizeof(DevTile));
+        if (cudaMemcpyAsync(w.d_tiles, w.h_tiles, tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice, w.st) !=
             cudaSuccess)
+            return false;
+    }
+    const size_t np = gin.size() + gout.size();
+    if (np) {
+        std::memcpy(w.h_pieces, gin.data(), gin.size() * sizeof(CopyPiece));
+        std::memcpy(w.h_pieces + gin.size(), gout.data(), gout.size() * sizeof(CopyPiece));
+        if (cudaMemcpyAsync(w.d_pieces, w.h_pieces, np * sizeof(CopyPiece), cudaMemcpyHostToDevice, w.st) !=
+            cudaSuccess)
+            return false;
+    }
+    if (cudaMemsetAsync(w.d_status, 0, sizeof(uint32_t), w.st) != cudaSuccess) return false;
+    w.host = !gin.empty();
+    if (w.host) {
+        if (cudaEventRecord(w.t0, w.st) != cudaSuccess ||
+            launch_copy_pieces(w.d_pieces, (uint32_t)gin.size(), w.st) != cudaSuccess ||
+            cudaEventRecord(w.t1, w.st) != cudaSuccess)
+            return false;
+    }
+    if (launch_tile_table(w.d_tiles, (uint32_t)tiles.size(), w.d_counter, w.d_err, (uint32_t)table.size(), w.st,
+                          w.d_status) != cudaSuccess)
         return false;
-    if (launch_tile_table(w.d_tiles, (uint32_t)tiles.size(), w.d_counter, w.d_err, (uint32_t)table.size(), w.st) !=
-        cudaSuccess)
-        return false;
-    if (cudaMemcpyAsync(w.h_err, w.d_err, table.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, w.st) !=
-        cudaSuccess)
+    if (w.host) {
+        if (cudaEventRecord(w.t2, w.st) != cudaSuccess ||
+            launch_copy_pieces(w.d_pieces + gin.size(), (uint32_t)gout.size(), w.st) != cudaSuccess ||
+            cudaEventRecord(w.t3, w.st) != cudaSuccess)
+            return false;
+    }
+    // the status word and the packets' error counts in one copy
+    if (cudaMemcpyAsync(w.h_back, w.d_status, 16 + table.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        w.st) != cudaSuccess)
         return false;
     return cudaEventRecord(w.ev, w.st) == cudaSuccess;
+}
+
+// Hand the wave's packets back with `status` (the counts only when HD_OK or a
+// timeout) and free its slot and budget.  Called with s->mu held.
+void complete_wave(hd_server *s, Wave &w, hd_status status, uint64_t t)
+{
+    const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(w.h_back + 4);
+    for (size_t j = 0; j < w.reqs.size(); ++j) {
+        hd_completion c;
+        c.tag = w.reqs[j].tag;
+        c.err_count = status == HD_OK ? cnt[j] : 0;
+        c.t_submit_ns = w.reqs[j].t_submit;
+        c.t_admit_ns = w.t_admit;
+        c.t_done_ns = t;
+        c.status = status;
+        s->done.push_back(c);
+    }
+    s->stats.completed += w.reqs.size();
+    s->resident -= w.bytes;
+    w.reqs.clear();
+    w.bytes = 0;
+    w.stage_used = 0;
+    w.host = false;
+    w.busy = false;
+    s->busy_waves.fetch_sub(1);
+}
+
+// After a CUDA failure the server stops admitting: every packet still
+// waiting completes with the server's error.  Called with s->mu held.
+void fail_pending(hd_server *s, uint64_t t)
+{
+    while (!s->pending.empty()) {
+        const Req &r = s->pending.front();
+        hd_completion c;
+        c.tag = r.tag;
+        c.err_count = 0;
+        c.t_submit_ns = r.t_submit;
+        c.t_admit_ns = 0;
+        c.t_done_ns = t;
+        c.status = s->error;
+        s->done.push_back(c);
+        s->stats.completed += 1;
+        s->pending.pop_front();
+    }
 }
 
 void scheduler(hd_server *s)
 {
     cudaSetDevice(s->device);
+    // after the last activity, poll for this long before sleeping on the
+    // condition variable, so that an arrival shortly after a completion does
+    // not pay a thread wake-up
+    constexpr uint64_t kSpinNs = 200000;
+    uint64_t last_active = now_ns();
     for (;;) {
         bool progress = false;
         // 1. completions
@@ -151,24 +277,26 @@ void scheduler(hd_server *s)
             const cudaError_t q = cudaEventQuery(w.ev);
             if (q == cudaErrorNotReady) continue;
             const uint64_t t = now_ns();
+            float a = 0.f, b = 0.f, c = 0.f;
+            const bool timed = q == cudaSuccess && w.host && cudaEventElapsedTime(&a, w.t0, w.t1) == cudaSuccess &&
+                               cudaEventElapsedTime(&b, w.t1, w.t2) == cudaSuccess &&
+                               cudaEventElapsedTime(&c, w.t2, w.t3) == cudaSuccess;
             std::lock_guard<std::mutex> lk(s->mu);
-            for (size_t j = 0; j < w.reqs.size(); ++j) {
-                hd_completion c;
-                c.tag = w.reqs[j].tag;
-                c.err_count = q == cudaSuccess ? w.h_err[j] : 0;
-                c.t_submit_ns = w.reqs[j].t_submit;
-                c.t_admit_ns = w.t_admit;
-                c.t_done_ns = t;
-                c.status = q == cudaSuccess ? HD_OK : HD_ERR_CUDA;
-                s->done.push_back(c);
+            hd_status st = HD_OK;
+            if (q != cudaSuccess) {
+                st = HD_ERR_CUDA;
+                s->error = HD_ERR_CUDA;
+            } else if (w.h_back[0] != 0) {
+                st = HD_ERR_TIMEOUT;  // a bounded wait of this wave's kernel ran out
             }
-            if (q != cudaSuccess) s->error = HD_ERR_CUDA;
-            s->stats.completed += w.reqs.size();
-            s->resident -= w.bytes;
-            w.reqs.clear();
-            w.bytes = 0;
-            w.busy = false;
-            s->busy_waves.fetch_sub(1);
+            if (timed) {
+                s->stats.host_waves += 1;
+                s->t_in_us += 1000.0 * a;
+                s->t_dec_us += 1000.0 * b;
+                s->t_out_us += 1000.0 * c;
+            }
+            complete_wave(s, w, st, t);
+            if (s->error != HD_OK) fail_pending(s, t);
             progress = true;
         }
         // 2. admission: fill every free slot from the FIFO, within the budget
@@ -176,13 +304,16 @@ void scheduler(hd_server *s)
             if (w.busy) continue;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
+                if (s->error != HD_OK) break;
                 uint64_t tiles = 0;
                 while (!s->pending.empty() && w.reqs.size() < s->cfg.max_wave_packets) {
                     const Req &r = s->pending.front();
                     if (s->resident + w.bytes + r.bytes > s->cfg.mem_cap_bytes) break;
                     if (!w.reqs.empty() && tiles + r.tiles > s->cfg.max_wave_tiles) break;
+                    if (r.host && w.stage_used + r.stage_b > s->cfg.host_staging_bytes) break;
                     tiles += r.tiles;
                     w.bytes += r.bytes;
+                    if (r.host) w.stage_used += r.stage_b;
                     w.reqs.push_back(r);
                     s->pending.pop_front();
                 }
@@ -198,71 +329,49 @@ void scheduler(hd_server *s)
             }
             w.t_admit = now_ns();
             if (!launch_wave(s, w)) {
+                // nothing of this wave is trusted: its packets fail now, and so does
+                // every packet still waiting (the server keeps the error)
+                const uint64_t t = now_ns();
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->error = HD_ERR_CUDA;
+                complete_wave(s, w, HD_ERR_CUDA, t);
+                fail_pending(s, t);
             }
             progress = true;
         }
-        if (progress) continue;
-        if (s->busy_waves.load() > 0) {
-            std::this_thread::yield();  // a wave is on the GPU: poll its event again soon
+        const uint64_t now = now_ns();
+        if (progress) {
+            last_active = now;
+            continue;
+        }
+        if (s->busy_waves.load() > 0 || now - last_active < kSpinNs) {
+            std::this_thread::yield();  // a wave is on the GPU, or an arrival may be near: poll again soon
             continue;
         }
         std::unique_lock<std::mutex> lk(s->mu);
         if (s->stop.load() && s->pending.empty()) break;
         s->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return s->stop.load() || !s->pending.empty(); });
+        last_active = now_ns();
     }
 }
 
-}  // namespace
-
-extern "C" {
-
-hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
+// Validate a host packet: its buffers must be pinned host memory that kernels
+// can reach (cudaPointerGetAttributes gives their device-accessible address).
+hd_status host_buffer(const void *p, const void **dev)
 {
-    if (!cfg || !out) return HD_ERR_NULL;
-    *out = nullptr;
-    if (cfg->max_waves == 0 || cfg->max_waves > 64 || cfg->max_wave_packets == 0 || cfg->max_wave_tiles == 0 ||
-        cfg->queue_capacity == 0 || cfg->mem_cap_bytes == 0)
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
         return HD_ERR_INVALID_ARG;
-    hd_server *s = new (std::nothrow) hd_server();
-    if (!s) return HD_ERR_CAPACITY;
-    s->cfg = *cfg;
-    std::memset(&s->stats, 0, sizeof(s->stats));
-    cudaGetDevice(&s->device);
-    s->waves.resize(cfg->max_waves);
-    for (Wave &w : s->waves) {
-        const size_t tb = (size_t)cfg->max_wave_tiles * sizeof(DevTile);
-        const size_t eb = (size_t)cfg->max_wave_packets * sizeof(unsigned long long);
-        char *d = nullptr;
-        if (cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&d, tb + 256 + eb) != cudaSuccess ||
-            cudaMallocHost(&w.h_tiles, tb) != cudaSuccess || cudaMallocHost(&w.h_err, eb) != cudaSuccess) {
-            if (d) cudaFree(d);
-            release_waves(s);
-            delete s;
-            return HD_ERR_CUDA;
-        }
-        w.d_tiles = reinterpret_cast<DevTile *>(d);
-        w.d_counter = reinterpret_cast<uint32_t *>(d + tb);
-        w.d_err = reinterpret_cast<unsigned long long *>(d + tb + 256);
     }
-    s->worker = std::thread(scheduler, s);
-    *out = s;
+    if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return HD_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(a.devicePointer) & 15u) != 0) return HD_ERR_ALIGN;
+    *dev = a.devicePointer;
     return HD_OK;
 }
 
-hd_status hd_server_submit(hd_server *s, const hd_packet *pkt, uint64_t tag)
+hd_status enqueue_req(hd_server *s, Req &r)
 {
-    if (!s || !pkt) return HD_ERR_NULL;
-    Req r;
-    hd_status err = HD_OK;
-    if (!packet_cost(*pkt, &r.bytes, &r.tiles, &err)) return err;
-    if (r.bytes > s->cfg.mem_cap_bytes || r.tiles > s->cfg.max_wave_tiles) return HD_ERR_CAPACITY;
-    r.pkt = *pkt;
-    if (!pkt->syndromes) r.pkt.syn_type = HD_SYN_NONE;
-    r.tag = tag;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->error != HD_OK) return s->error;
@@ -278,56 +387,8 @@ hd_status hd_server_submit(hd_server *s, const hd_packet *pkt, uint64_t tag)
     return HD_OK;
 }
 
-hd_status hd_server_poll(hd_server *s, hd_completion *out, uint32_t max, uint32_t *count)
-{
-    if (!s || !count || (max > 0 && !out)) return HD_ERR_NULL;
-    std::lock_guard<std::mutex> lk(s->mu);
-    uint32_t c = 0;
-    while (c < max && !s->done.empty()) {
-        out[c++] = s->done.front();
-        s->done.pop_front();
-    }
-    *count = c;
-    return s->error;
-}
-
-hd_status hd_server_drain(hd_server *s, uint64_t timeout_ns)
-{
-    if (!s) return HD_ERR_NULL;
-    const uint64_t t0 = now_ns();
-    for (;;) {
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (s->error != HD_OK) return s->error;
-            if (s->pending.empty() && s->busy_waves.load() == 0) return HD_OK;
-        }
-        if (now_ns() - t0 > timeout_ns) return HD_ERR_TIMEOUT;
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
-}
-
-hd_status hd_server_get_stats(hd_server *s, hd_server_stats *stats)
-{
-    if (!s || !stats) return HD_ERR_NULL;
-    std::lock_guard<std::mutex> lk(s->mu);
-    *stats = s->stats;
-    stats->mean_wave_packets = s->stats.waves ? (double)s->wave_packets_sum / (double)s->stats.waves : 0.0;
-    return HD_OK;
-}
-
-void hd_server_destroy(hd_server *s)
-{
-    if (!s) return;
-    s->stop.store(true);
-    s->cv.notify_all();
-    // let the scheduler finish what was admitted and submitted
-    if (s->worker.joinable()) s->worker.join();
-    release_waves(s);
-    delete s;
-}
-
-hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *pkts, const double *arrival_s, uint32_t num,
-                         hd_completion *completions, hd_server_stats *stats)
+hd_status serve_trace(const hd_server_config *cfg, const hd_packet *pkts, const double *arrival_s, uint32_t num,
+                      hd_completion *completions, hd_server_stats *stats, bool host)
 {
     if (!cfg || (num > 0 && (!pkts || !arrival_s || !completions)) || !stats) return HD_ERR_NULL;
     for (uint32_t j = 1; j < num; ++j)
@@ -360,7 +421,7 @@ hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *pkts, con
             else std::this_thread::yield();
         }
         for (;;) {
-            const hd_status e = hd_server_submit(s, &pkts[j], j);
+            const hd_status e = host ? hd_server_submit_host(s, &pkts[j], j) : hd_server_submit(s, &pkts[j], j);
             if (e == HD_OK) break;
             if (e != HD_ERR_CAPACITY) {
                 rc = e;
@@ -401,6 +462,178 @@ hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *pkts, con
     stats->duration_s = num ? (double)(last - first) * 1e-9 : 0.0;
     stats->backpressure_waits = backpressure;
     return HD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
+{
+    if (!cfg || !out) return HD_ERR_NULL;
+    *out = nullptr;
+    if (cfg->max_waves == 0 || cfg->max_waves > 64 || cfg->max_wave_packets == 0 || cfg->max_wave_tiles == 0 ||
+        cfg->queue_capacity == 0 || cfg->mem_cap_bytes == 0 || cfg->host_staging_bytes > (1ull << 40))
+        return HD_ERR_INVALID_ARG;
+    hd_server *s = new (std::nothrow) hd_server();
+    if (!s) return HD_ERR_CAPACITY;
+    s->cfg = *cfg;
+    std::memset(&s->stats, 0, sizeof(s->stats));
+    cudaGetDevice(&s->device);
+    // pieces of a wave: at most one per kPieceBytes of staging plus three
+    // partial ones (input, output, syndromes) per packet
+    s->pieces_cap = cfg->host_staging_bytes ? cfg->host_staging_bytes / kPieceBytes + 3ull * cfg->max_wave_packets : 0;
+    const size_t tb = ((size_t)cfg->max_wave_tiles * sizeof(DevTile) + 255) / 256 * 256;
+    const size_t pb = ((size_t)s->pieces_cap * sizeof(CopyPiece) + 255) / 256 * 256;
+    const size_t bb = 16 + (size_t)cfg->max_wave_packets * sizeof(unsigned long long);  // status word + counts
+    const size_t sb = (size_t)((cfg->host_staging_bytes + 255) / 256 * 256);
+    s->waves.resize(cfg->max_waves);
+    bool ok = true;
+    for (Wave &w : s->waves) {
+        ok = cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&w.t0) == cudaSuccess && cudaEventCreate(&w.t1) == cudaSuccess &&
+             cudaEventCreate(&w.t2) == cudaSuccess && cudaEventCreate(&w.t3) == cudaSuccess &&
+             cudaMalloc(&w.dmem, tb + pb + 256 + (bb + 255) / 256 * 256 + sb) == cudaSuccess &&
+             cudaMallocHost(&w.h_tiles, tb) == cudaSuccess && cudaMallocHost(&w.h_back, bb) == cudaSuccess &&
+             (pb == 0 || cudaMallocHost(&w.h_pieces, pb) == cudaSuccess);
+        if (!ok) break;
+        char *d = w.dmem;
+        w.d_tiles = reinterpret_cast<DevTile *>(d);
+        w.d_pieces = reinterpret_cast<CopyPiece *>(d + tb);
+        w.d_counter = reinterpret_cast<uint32_t *>(d + tb + pb);
+        w.d_status = reinterpret_cast<uint32_t *>(d + tb + pb + 256);
+        w.d_err = reinterpret_cast<unsigned long long *>(d + tb + pb + 256 + 16);
+        w.d_stage = reinterpret_cast<unsigned char *>(d + tb + pb + 256 + (bb + 255) / 256 * 256);
+        // one-time set-up of the batch kernel (attributes, occupancy, the n = 7
+        // table) now, so that the first wave pays none of it
+        ok = launch_tile_table(w.d_tiles, 0, w.d_counter, nullptr, 0, w.st, w.d_status) == cudaSuccess &&
+             cudaStreamSynchronize(w.st) == cudaSuccess;
+        if (!ok) break;
+    }
+    if (!ok) {
+        release_waves(s);
+        delete s;
+        return HD_ERR_CUDA;
+    }
+    s->worker = std::thread(scheduler, s);
+    *out = s;
+    return HD_OK;
+}
+
+hd_status hd_server_submit(hd_server *s, const hd_packet *pkt, uint64_t tag)
+{
+    if (!s || !pkt) return HD_ERR_NULL;
+    Req r;
+    hd_status err = HD_OK;
+    if (!packet_cost(*pkt, &r.bytes, &r.tiles, &err)) return err;
+    if (r.bytes > s->cfg.mem_cap_bytes || r.tiles > s->cfg.max_wave_tiles) return HD_ERR_CAPACITY;
+    r.pkt = *pkt;
+    if (!pkt->syndromes) r.pkt.syn_type = HD_SYN_NONE;
+    r.tag = tag;
+    return enqueue_req(s, r);
+}
+
+hd_status hd_server_submit_host(hd_server *s, const hd_packet *pkt, uint64_t tag)
+{
+    if (!s || !pkt) return HD_ERR_NULL;
+    if (s->cfg.host_staging_bytes == 0) return HD_ERR_INVALID_ARG;
+    Req r;
+    hd_status err = HD_OK;
+    if (!packet_cost(*pkt, &r.bytes, &r.tiles, &err)) return err;
+    r.pkt = *pkt;
+    if (!pkt->syndromes) r.pkt.syn_type = HD_SYN_NONE;
+    r.tag = tag;
+    r.host = true;
+    const uint64_t N = pkt->num_codewords, m = (uint64_t)code_m(pkt->n), k = pkt->n - m;
+    r.in_b = words_for_bits(N * pkt->n) * 4;
+    r.out_b = words_for_bits(N * k) * 4;
+    r.syn_b = N * (r.pkt.syn_type == HD_SYN_U16 ? 2u : (r.pkt.syn_type == HD_SYN_U8 ? 1u : 0u));
+    r.stage_b = round16(r.in_b) + round16(r.out_b) + round16(r.syn_b);
+    if (N > 0) {
+        void *dv = nullptr;
+        if ((err = host_buffer(pkt->in, &r.dev_in)) != HD_OK) return err;
+        if ((err = host_buffer(pkt->out, const_cast<const void **>(&dv))) != HD_OK) return err;
+        r.dev_out = dv;
+        if (r.syn_b) {
+            if ((err = host_buffer(pkt->syndromes, const_cast<const void **>(&dv))) != HD_OK) return err;
+            r.dev_syn = dv;
+        }
+    }
+    if (r.bytes > s->cfg.mem_cap_bytes || r.tiles > s->cfg.max_wave_tiles || r.stage_b > s->cfg.host_staging_bytes)
+        return HD_ERR_CAPACITY;
+    return enqueue_req(s, r);
+}
+
+hd_status hd_server_inject_launch_failures(hd_server *s, uint32_t count)
+{
+    if (!s) return HD_ERR_NULL;
+    s->inject_failures.store(count);
+    return HD_OK;
+}
+
+hd_status hd_server_poll(hd_server *s, hd_completion *out, uint32_t max, uint32_t *count)
+{
+    if (!s || !count || (max > 0 && !out)) return HD_ERR_NULL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    uint32_t c = 0;
+    while (c < max && !s->done.empty()) {
+        out[c++] = s->done.front();
+        s->done.pop_front();
+    }
+    *count = c;
+    return s->error;
+}
+
+hd_status hd_server_drain(hd_server *s, uint64_t timeout_ns)
+{
+    if (!s) return HD_ERR_NULL;
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->error != HD_OK) return s->error;
+            if (s->pending.empty() && s->busy_waves.load() == 0) return HD_OK;
+        }
+        if (now_ns() - t0 > timeout_ns) return HD_ERR_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+hd_status hd_server_get_stats(hd_server *s, hd_server_stats *stats)
+{
+    if (!s || !stats) return HD_ERR_NULL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *stats = s->stats;
+    stats->mean_wave_packets = s->stats.waves ? (double)s->wave_packets_sum / (double)s->stats.waves : 0.0;
+    const double hw = (double)s->stats.host_waves;
+    stats->mean_t_in_us = hw > 0 ? s->t_in_us / hw : 0.0;
+    stats->mean_t_decode_us = hw > 0 ? s->t_dec_us / hw : 0.0;
+    stats->mean_t_out_us = hw > 0 ? s->t_out_us / hw : 0.0;
+    return HD_OK;
+}
+
+void hd_server_destroy(hd_server *s)
+{
+    if (!s) return;
+    s->stop.store(true);
+    s->cv.notify_all();
+    // let the scheduler finish what was admitted and submitted
+    if (s->worker.joinable()) s->worker.join();
+    release_waves(s);
+    delete s;
+}
+
+hd_status hd_serve_trace(const hd_server_config *cfg, const hd_packet *pkts, const double *arrival_s, uint32_t num,
+                         hd_completion *completions, hd_server_stats *stats)
+{
+    return serve_trace(cfg, pkts, arrival_s, num, completions, stats, false);
+}
+
+hd_status hd_serve_trace_host(const hd_server_config *cfg, const hd_packet *pkts, const double *arrival_s,
+                              uint32_t num, hd_completion *completions, hd_server_stats *stats)
+{
+    return serve_trace(cfg, pkts, arrival_s, num, completions, stats, true);
 }
 
 }  // extern "C"

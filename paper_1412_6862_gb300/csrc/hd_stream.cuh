@@ -52,7 +52,9 @@ struct ChunkGeom {
     static constexpr int H = 32 / G;                                  // threads per 32-codeword tile
     static constexpr int TEAMS = LANES / H;                           // tiles per warp chunk
     static constexpr int SB = SYN == 2 ? 2 : 1;                       // syndrome bytes (packing width)
-    static constexpr bool WIDE = (SB == 1 && C::m + (XH ? 1 : 0) == 8);  // u8 lanes may use bit 7
+    // syndrome values of 8 or more bits (m = 8, or SECDED's s | P << m with m >= 7) leave no
+    // free top bit in a byte lane: count them by compare instead of the carry trick
+    static constexpr bool WIDE = (SB == 1 && C::m + (XH ? 1 : 0) >= 8);
     static constexpr int GK = G * C::k;                               // output bits per thread
     static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
     static constexpr int R = (G * L + 31) / 32;                       // input words per thread after re-alignment

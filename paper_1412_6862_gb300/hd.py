@@ -73,7 +73,7 @@ class HostJob(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     """Mirror of hd_server_config."""
     _fields_ = [("max_waves", _u32), ("max_wave_packets", _u32), ("max_wave_tiles", _u32),
-                ("queue_capacity", _u32), ("mem_cap_bytes", _u64)]
+                ("queue_capacity", _u32), ("mem_cap_bytes", _u64), ("host_staging_bytes", _u64)]
 
 
 class Completion(ctypes.Structure):
@@ -87,7 +87,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("waves", _u64),
                 ("max_resident_bytes", _u64), ("mean_wave_packets", _c.c_double), ("p50_latency_us", _c.c_double),
                 ("p99_latency_us", _c.c_double), ("max_latency_us", _c.c_double), ("duration_s", _c.c_double),
-                ("backpressure_waits", _u64)]
+                ("backpressure_waits", _u64), ("host_waves", _u64), ("mean_t_in_us", _c.c_double),
+                ("mean_t_decode_us", _c.c_double), ("mean_t_out_us", _c.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -118,11 +119,14 @@ SIGNATURES = {
     "hd_batch_tiles": (_i32, [_PKP, _u32, _c.POINTER(_u64)]),
     "hd_server_create": (_i32, [_SCP, _c.POINTER(_vp)]),
     "hd_server_submit": (_i32, [_vp, _PKP, _u64]),
+    "hd_server_submit_host": (_i32, [_vp, _PKP, _u64]),
+    "hd_server_inject_launch_failures": (_i32, [_vp, _u32]),
     "hd_server_poll": (_i32, [_vp, _CMP, _u32, _c.POINTER(_u32)]),
     "hd_server_drain": (_i32, [_vp, _u64]),
     "hd_server_get_stats": (_i32, [_vp, _SSP]),
     "hd_server_destroy": (None, [_vp]),
     "hd_serve_trace": (_i32, [_SCP, _PKP, _c.POINTER(_c.c_double), _u32, _CMP, _SSP]),
+    "hd_serve_trace_host": (_i32, [_SCP, _PKP, _c.POINTER(_c.c_double), _u32, _CMP, _SSP]),
     "hd_encode": (_i32, [_vp, _u32, _u64, _vp, _vp]),
     "hd_short_params": (_i32, [_u32, _c.POINTER(_u32), _c.POINTER(_u32)]),
     "hd_segment_params": (_i32, [_u32, _u32, _c.POINTER(_u32), _c.POINTER(_u32), _c.POINTER(_u32)]),
@@ -350,18 +354,21 @@ def hd_batch_tiles(table, num_packets: int) -> int:
 
 
 def server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=65536, queue_capacity=1 << 16,
-                  mem_cap_bytes=4 << 30) -> ServerConfig:
-    return ServerConfig(max_waves, max_wave_packets, max_wave_tiles, queue_capacity, mem_cap_bytes)
+                  mem_cap_bytes=4 << 30, host_staging_bytes=0) -> ServerConfig:
+    return ServerConfig(max_waves, max_wave_packets, max_wave_tiles, queue_capacity, mem_cap_bytes,
+                        host_staging_bytes)
 
 
-def hd_serve_trace(cfg: ServerConfig, table, arrival_s, num: int):
-    """Replay an arrival trace; returns (completions array, stats dict)."""
+def hd_serve_trace(cfg: ServerConfig, table, arrival_s, num: int, host: bool = False):
+    """Replay an arrival trace (host=True: the packets' buffers are pinned host
+    memory, hd_serve_trace_host); returns (completions array, stats dict)."""
     import numpy as np
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
     comps = (Completion * max(1, num))()
     st = ServerStats()
-    check(lib().hd_serve_trace(ctypes.byref(cfg), table, arr.ctypes.data_as(_c.POINTER(_c.c_double)), num, comps,
-                               ctypes.byref(st)), "hd_serve_trace")
+    fn = lib().hd_serve_trace_host if host else lib().hd_serve_trace
+    check(fn(ctypes.byref(cfg), table, arr.ctypes.data_as(_c.POINTER(_c.c_double)), num, comps, ctypes.byref(st)),
+          "hd_serve_trace_host" if host else "hd_serve_trace")
     return comps, st.as_dict()
 
 
@@ -377,6 +384,14 @@ class Server:
     def submit(self, in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type, tag) -> int:
         pk = Packet(in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type if syn_ptr else SYN_NONE)
         return lib().hd_server_submit(self.handle, ctypes.byref(pk), tag)
+
+    def submit_host(self, in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type, tag) -> int:
+        """Queue a packet whose buffers are pinned host memory."""
+        pk = Packet(in_ptr, out_ptr, syn_ptr, num_codewords, n, syn_type if syn_ptr else SYN_NONE)
+        return lib().hd_server_submit_host(self.handle, ctypes.byref(pk), tag)
+
+    def inject_launch_failures(self, count: int) -> None:
+        check(lib().hd_server_inject_launch_failures(self.handle, count), "hd_server_inject_launch_failures")
 
     def poll(self, max_n: int = 4096):
         buf = (Completion * max_n)()
