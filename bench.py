@@ -565,6 +565,10 @@ def time_graph(dev, calls, rounds, warm=2):
     return a.elapsed_time(b) / 1e3 / (rounds * len(calls))
 
 
+# (n, syndrome type) -> the autotuner's choice in this process
+TUNED = {}
+
+
 # Every benchmark configuration of a single code (the codes and error rates the
 # workload names): (label, n, codewords, [(p1, p2)], syndrome bytes).
 PER_CODE = (
@@ -588,11 +592,16 @@ def run_per_code(dev, args, peak):
     from paper_1412_6862_gb300 import hd, synth
     res = []
     codes = {int(c) for c in args.per_code_codes.split(",")} if args.per_code_codes else None
+    stream = torch.cuda.current_stream(dev)
     for label, n, N, rates, sb in PER_CODE:
         if codes is not None and n not in codes:
             continue
         m, k = code_params(n)
         syn_t = hd.SYN_U8 if sb == 1 else hd.SYN_U16
+        # hd_autotune on this code, size and syndrome type (kept from the sweep when already tuned)
+        if not args.no_autotune and (n, syn_t) not in TUNED:
+            TUNED[(n, syn_t)] = hd.hd_autotune(n, syn_t, N, 5, stream)
+        cfg = hd.hd_variant_current(n, syn_t)
         gen = torch.Generator(device=dev)
         gen.manual_seed(2000 + n)
         data = torch.randint(-2**31, 2**31 - 1, (hd.words_for(N * k) + 4,), dtype=torch.int32, device=dev,
@@ -624,6 +633,8 @@ def run_per_code(dev, args, peak):
             t = time_graph(dev, [call(b) for b in sets], rounds)
             errs = [int(b[3].item()) for b in sets]
             res.append({"config": label, "n": n, "codewords": N, "p1": p1, "p2": p2,
+                        "kernel": {key: cfg[key] for key in ("threads", "stages", "codewords_per_thread", "inplace",
+                                                             "table_lookup")},
                         "us_per_launch": t * 1e6, "gbps": N * k / t / 1e9, "hbm_frac": nbytes / t / 1e9 / peak,
                         "algorithmic_bytes": nbytes, "buffer_sets": nsets, "l2_resident": bool(l2_resident),
                         "err_count": errs[0], "injected_events": int(ev.num_events),
@@ -954,6 +965,7 @@ def run_ours(args):
             info = hd.hd_variant_current(n, hd.SYN_U8)
         elif not args.no_autotune:
             info = hd.hd_autotune(n, hd.SYN_U8, SWEEP_N, 5, stream_h)
+            TUNED[(n, hd.SYN_U8)] = info
         else:
             continue
         tuned[str(n)] = {key: info[key] for key in ("threads", "stages", "codewords_per_thread", "inplace",

@@ -444,8 +444,8 @@ typedef struct {
     double p50_latency_us, p99_latency_us, max_latency_us;
     double duration_s;           /* first arrival to last completion */
     uint64_t backpressure_waits; /* submissions retried because the queue was full */
-    /* waves that carried host packets, and their mean stage times measured by CUDA events on the
-       slot's stream: gather (T_PS), batched decode (T_DKE), scatter (T_PR) */
+    /* waves that carried host packets, and the mean stage times of one in four of them, measured by
+       CUDA events on the slot's stream: gather (T_PS), batched decode (T_DKE), scatter (T_PR) */
     uint64_t host_waves;
     double mean_t_in_us, mean_t_decode_us, mean_t_out_us;
 } hd_server_stats;

@@ -557,16 +557,20 @@ cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
     return g->grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
-cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *err_counts, cudaStream_t st)
+cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *err_counts, cudaStream_t st,
+                         bool clear = true)
 {
     const BatchVariant &v = batch_variants()[g.variant];
     const int grid = g.grid;
     uint32_t *status = g.status;
-    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    if (err_counts) {
-        e = cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * p->num_packets, st);
+    cudaError_t e = cudaSuccess;
+    if (clear) {
+        e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
+        if (err_counts) {
+            e = cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * p->num_packets, st);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (p->num_tiles == 0) return cudaSuccess;
     v.launch(grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15);
@@ -597,7 +601,8 @@ hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::ve
 }
 
 cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32_t *d_counter,
-                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st, uint32_t *status)
+                              unsigned long long *d_err, uint32_t num_packets, cudaStream_t st, uint32_t *status,
+                              bool clear)
 {
     hd_plan p;
     p.num_packets = num_packets;
@@ -607,7 +612,7 @@ cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32
     LaunchGeom geom;
     cudaError_t e = prepare_plan(&p, &geom, st);
     if (status != nullptr) geom.status = status;
-    if (e == cudaSuccess) e = enqueue_plan(&p, geom, d_err, st);
+    if (e == cudaSuccess) e = enqueue_plan(&p, geom, d_err, st, clear);
     if (e == cudaSuccess && num_tiles) count_launch();
     return e;
 }

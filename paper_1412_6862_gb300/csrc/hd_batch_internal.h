@@ -64,10 +64,12 @@ hd_status build_tile_table(const hd_packet *table, uint32_t num_packets, std::ve
 // kernel in its default configuration.  Host-side setup (kernel attributes,
 // occupancy, status word) happens on the first call per device.  A timeout
 // is latched into `status` (device) when not NULL, else into the device's
-// status word.  num_tiles = 0 performs only the set-up and the clears.
+// status word.  num_tiles = 0 performs only the set-up and the clears.  With
+// clear = false the caller has already zeroed the claim counter and the error
+// counters (for example in the same copy that uploaded the table).
 cudaError_t launch_tile_table(const DevTile *d_tiles, uint32_t num_tiles, uint32_t *d_counter,
                               unsigned long long *d_err, uint32_t num_packets, cudaStream_t st,
-                              uint32_t *status = nullptr);
+                              uint32_t *status = nullptr, bool clear = true);
 
 // A contiguous copy of at most kPieceBytes between two 16-byte aligned
 // addresses that kernels can dereference (device memory, or pinned host memory

@@ -81,27 +81,33 @@ struct Req {
 
 inline uint64_t round16(uint64_t b) { return (b + 15) & ~15ull; }
 
+// A wave's table region, in device memory and in its pinned upload image
+// alike: the status word (offset 0) and the claim counter (offset 16), the
+// packets' error counts (offset 32), the tiles (64-byte aligned) and the copy
+// pieces.  Status, counter and counts are zero in the image, so that one copy
+// uploads the tables and clears everything the kernels accumulate into.
+constexpr size_t kOffCounter = 16, kOffErr = 32;
+inline size_t tiles_offset(size_t packets) { return (kOffErr + packets * 8 + 63) & ~size_t(63); }
+
+// Stage times are taken (four timing events) on one host wave in this many.
+constexpr uint64_t kTimeEvery = 4;
+
 struct Wave {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;                // completion
-    cudaEvent_t t0 = nullptr, t1 = nullptr;  // stage timing of host waves: before and after the gather,
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // stage timing of sampled host waves: before and after the gather,
     cudaEvent_t t2 = nullptr, t3 = nullptr;  // after the decode and after the scatter
-    char *dmem = nullptr;                    // one allocation: tiles, pieces, counter, status + counts, staging
-    DevTile *d_tiles = nullptr;
-    CopyPiece *d_pieces = nullptr;
-    uint32_t *d_counter = nullptr;
-    uint32_t *d_status = nullptr;            // the wave's status word, followed by the error counts
-    unsigned long long *d_err = nullptr;
+    char *dmem = nullptr;                    // the table region, then the staging of host packets
     unsigned char *d_stage = nullptr;
-    DevTile *h_tiles = nullptr;              // pinned staging of the tile table
-    CopyPiece *h_pieces = nullptr;           // pinned staging of the copy pieces
-    uint32_t *h_back = nullptr;              // pinned: status word (16 bytes), then the error counts
+    char *h_up = nullptr;                    // pinned upload image of the table region
+    char *h_back = nullptr;                  // pinned: status word, counter, error counts
     std::vector<Req> reqs;
     uint64_t bytes = 0;
     uint64_t stage_used = 0;
     uint64_t t_admit = 0;
     bool busy = false;
-    bool host = false;                       // carries host packets (timed stages)
+    bool host = false;                       // carries host packets
+    bool timed = false;                      // its stages are timed
 };
 
 }  // namespace
@@ -126,7 +132,10 @@ struct hd_server {
     std::atomic<uint32_t> inject_failures{0};  // test hook: wave launches to fail on the host
     hd_status error = HD_OK;
     uint64_t pieces_cap = 0;                    // copy pieces per wave
-    double t_in_us = 0, t_dec_us = 0, t_out_us = 0;  // summed stage times of host waves
+    size_t table_cap = 0;                       // bytes of a wave's table region
+    uint64_t host_launched = 0;                 // host waves launched (every kTimeEvery-th is timed)
+    uint64_t timed_waves = 0;
+    double t_in_us = 0, t_dec_us = 0, t_out_us = 0;  // summed stage times of the timed host waves
 };
 
 namespace {
@@ -139,8 +148,7 @@ void release_waves(hd_server *s)
             if (e) cudaEventDestroy(e);
         if (w.st) cudaStreamDestroy(w.st);
         if (w.dmem) cudaFree(w.dmem);
-        if (w.h_tiles) cudaFreeHost(w.h_tiles);
-        if (w.h_pieces) cudaFreeHost(w.h_pieces);
+        if (w.h_up) cudaFreeHost(w.h_up);
         if (w.h_back) cudaFreeHost(w.h_back);
         w = Wave();
     }
@@ -179,40 +187,40 @@ bool launch_wave(hd_server *s, Wave &w)
     if (build_tile_table(table.data(), (uint32_t)table.size(), tiles, nullptr) != HD_OK) return false;
     if (tiles.size() > s->cfg.max_wave_tiles) return false;  // admission bounds the tiles; never reached
     if (gin.size() + gout.size() > s->pieces_cap) return false;  // bounded by the staging; never reached
-    if (!tiles.empty()) {
-        std::memcpy(w.h_tiles, tiles.data(), tiles.size() * sizeof(DevTile));
-        if (cudaMemcpyAsync(w.d_tiles, w.h_tiles, tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice, w.st) !=
-            cudaSuccess)
-            return false;
-    }
-    const size_t np = gin.size() + gout.size();
-    if (np) {
-        std::memcpy(w.h_pieces, gin.data(), gin.size() * sizeof(CopyPiece));
-        std::memcpy(w.h_pieces + gin.size(), gout.data(), gout.size() * sizeof(CopyPiece));
-        if (cudaMemcpyAsync(w.d_pieces, w.h_pieces, np * sizeof(CopyPiece), cudaMemcpyHostToDevice, w.st) !=
-            cudaSuccess)
-            return false;
-    }
-    if (cudaMemsetAsync(w.d_status, 0, sizeof(uint32_t), w.st) != cudaSuccess) return false;
+    // the upload image: zeroed status, counter and counts, then tiles and pieces
+    const size_t toff = tiles_offset(table.size());
+    const size_t poff = toff + tiles.size() * sizeof(DevTile);
+    const size_t used = poff + (gin.size() + gout.size()) * sizeof(CopyPiece);
+    std::memset(w.h_up, 0, toff);
+    if (!tiles.empty()) std::memcpy(w.h_up + toff, tiles.data(), tiles.size() * sizeof(DevTile));
+    if (!gin.empty()) std::memcpy(w.h_up + poff, gin.data(), gin.size() * sizeof(CopyPiece));
+    if (!gout.empty())
+        std::memcpy(w.h_up + poff + gin.size() * sizeof(CopyPiece), gout.data(), gout.size() * sizeof(CopyPiece));
+    if (cudaMemcpyAsync(w.dmem, w.h_up, used, cudaMemcpyHostToDevice, w.st) != cudaSuccess) return false;
+    uint32_t *d_status = reinterpret_cast<uint32_t *>(w.dmem);
+    const CopyPiece *d_pieces = reinterpret_cast<const CopyPiece *>(w.dmem + poff);
     w.host = !gin.empty();
+    w.timed = w.host && (s->host_launched++ % kTimeEvery) == 0;
     if (w.host) {
-        if (cudaEventRecord(w.t0, w.st) != cudaSuccess ||
-            launch_copy_pieces(w.d_pieces, (uint32_t)gin.size(), w.st) != cudaSuccess ||
-            cudaEventRecord(w.t1, w.st) != cudaSuccess)
+        if ((w.timed && cudaEventRecord(w.t0, w.st) != cudaSuccess) ||
+            launch_copy_pieces(d_pieces, (uint32_t)gin.size(), w.st) != cudaSuccess ||
+            (w.timed && cudaEventRecord(w.t1, w.st) != cudaSuccess))
             return false;
     }
-    if (launch_tile_table(w.d_tiles, (uint32_t)tiles.size(), w.d_counter, w.d_err, (uint32_t)table.size(), w.st,
-                          w.d_status) != cudaSuccess)
+    if (launch_tile_table(reinterpret_cast<const DevTile *>(w.dmem + toff), (uint32_t)tiles.size(),
+                          reinterpret_cast<uint32_t *>(w.dmem + kOffCounter),
+                          reinterpret_cast<unsigned long long *>(w.dmem + kOffErr), (uint32_t)table.size(), w.st,
+                          d_status, false) != cudaSuccess)
         return false;
     if (w.host) {
-        if (cudaEventRecord(w.t2, w.st) != cudaSuccess ||
-            launch_copy_pieces(w.d_pieces + gin.size(), (uint32_t)gout.size(), w.st) != cudaSuccess ||
-            cudaEventRecord(w.t3, w.st) != cudaSuccess)
+        if ((w.timed && cudaEventRecord(w.t2, w.st) != cudaSuccess) ||
+            launch_copy_pieces(d_pieces + gin.size(), (uint32_t)gout.size(), w.st) != cudaSuccess ||
+            (w.timed && cudaEventRecord(w.t3, w.st) != cudaSuccess))
             return false;
     }
     // the status word and the packets' error counts in one copy
-    if (cudaMemcpyAsync(w.h_back, w.d_status, 16 + table.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                        w.st) != cudaSuccess)
+    if (cudaMemcpyAsync(w.h_back, w.dmem, kOffErr + table.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, w.st) != cudaSuccess)
         return false;
     return cudaEventRecord(w.ev, w.st) == cudaSuccess;
 }
@@ -221,7 +229,7 @@ bool launch_wave(hd_server *s, Wave &w)
 // timeout) and free its slot and budget.  Called with s->mu held.
 void complete_wave(hd_server *s, Wave &w, hd_status status, uint64_t t)
 {
-    const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(w.h_back + 4);
+    const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(w.h_back + kOffErr);
     for (size_t j = 0; j < w.reqs.size(); ++j) {
         hd_completion c;
         c.tag = w.reqs[j].tag;
@@ -238,6 +246,7 @@ void complete_wave(hd_server *s, Wave &w, hd_status status, uint64_t t)
     w.bytes = 0;
     w.stage_used = 0;
     w.host = false;
+    w.timed = false;
     w.busy = false;
     s->busy_waves.fetch_sub(1);
 }
@@ -278,7 +287,7 @@ void scheduler(hd_server *s)
             if (q == cudaErrorNotReady) continue;
             const uint64_t t = now_ns();
             float a = 0.f, b = 0.f, c = 0.f;
-            const bool timed = q == cudaSuccess && w.host && cudaEventElapsedTime(&a, w.t0, w.t1) == cudaSuccess &&
+            const bool timed = q == cudaSuccess && w.timed && cudaEventElapsedTime(&a, w.t0, w.t1) == cudaSuccess &&
                                cudaEventElapsedTime(&b, w.t1, w.t2) == cudaSuccess &&
                                cudaEventElapsedTime(&c, w.t2, w.t3) == cudaSuccess;
             std::lock_guard<std::mutex> lk(s->mu);
@@ -286,11 +295,12 @@ void scheduler(hd_server *s)
             if (q != cudaSuccess) {
                 st = HD_ERR_CUDA;
                 s->error = HD_ERR_CUDA;
-            } else if (w.h_back[0] != 0) {
+            } else if (*reinterpret_cast<const uint32_t *>(w.h_back) != 0) {
                 st = HD_ERR_TIMEOUT;  // a bounded wait of this wave's kernel ran out
             }
+            if (w.host) s->stats.host_waves += 1;
             if (timed) {
-                s->stats.host_waves += 1;
+                s->timed_waves += 1;
                 s->t_in_us += 1000.0 * a;
                 s->t_dec_us += 1000.0 * b;
                 s->t_out_us += 1000.0 * c;
@@ -483,10 +493,11 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
     // pieces of a wave: at most one per kPieceBytes of staging plus three
     // partial ones (input, output, syndromes) per packet
     s->pieces_cap = cfg->host_staging_bytes ? cfg->host_staging_bytes / kPieceBytes + 3ull * cfg->max_wave_packets : 0;
-    const size_t tb = ((size_t)cfg->max_wave_tiles * sizeof(DevTile) + 255) / 256 * 256;
-    const size_t pb = ((size_t)s->pieces_cap * sizeof(CopyPiece) + 255) / 256 * 256;
-    const size_t bb = 16 + (size_t)cfg->max_wave_packets * sizeof(unsigned long long);  // status word + counts
+    s->table_cap = tiles_offset(cfg->max_wave_packets) + (size_t)cfg->max_wave_tiles * sizeof(DevTile) +
+                   (size_t)s->pieces_cap * sizeof(CopyPiece);
+    const size_t tr = (s->table_cap + 255) / 256 * 256;
     const size_t sb = (size_t)((cfg->host_staging_bytes + 255) / 256 * 256);
+    const size_t bb = kOffErr + (size_t)cfg->max_wave_packets * sizeof(unsigned long long);
     s->waves.resize(cfg->max_waves);
     bool ok = true;
     for (Wave &w : s->waves) {
@@ -494,20 +505,15 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
              cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreate(&w.t0) == cudaSuccess && cudaEventCreate(&w.t1) == cudaSuccess &&
              cudaEventCreate(&w.t2) == cudaSuccess && cudaEventCreate(&w.t3) == cudaSuccess &&
-             cudaMalloc(&w.dmem, tb + pb + 256 + (bb + 255) / 256 * 256 + sb) == cudaSuccess &&
-             cudaMallocHost(&w.h_tiles, tb) == cudaSuccess && cudaMallocHost(&w.h_back, bb) == cudaSuccess &&
-             (pb == 0 || cudaMallocHost(&w.h_pieces, pb) == cudaSuccess);
+             cudaMalloc(&w.dmem, tr + sb) == cudaSuccess && cudaMallocHost(&w.h_up, s->table_cap) == cudaSuccess &&
+             cudaMallocHost(&w.h_back, bb) == cudaSuccess;
         if (!ok) break;
-        char *d = w.dmem;
-        w.d_tiles = reinterpret_cast<DevTile *>(d);
-        w.d_pieces = reinterpret_cast<CopyPiece *>(d + tb);
-        w.d_counter = reinterpret_cast<uint32_t *>(d + tb + pb);
-        w.d_status = reinterpret_cast<uint32_t *>(d + tb + pb + 256);
-        w.d_err = reinterpret_cast<unsigned long long *>(d + tb + pb + 256 + 16);
-        w.d_stage = reinterpret_cast<unsigned char *>(d + tb + pb + 256 + (bb + 255) / 256 * 256);
+        w.d_stage = reinterpret_cast<unsigned char *>(w.dmem + tr);
         // one-time set-up of the batch kernel (attributes, occupancy, the n = 7
         // table) now, so that the first wave pays none of it
-        ok = launch_tile_table(w.d_tiles, 0, w.d_counter, nullptr, 0, w.st, w.d_status) == cudaSuccess &&
+        ok = launch_tile_table(reinterpret_cast<const DevTile *>(w.dmem + tiles_offset(0)), 0,
+                               reinterpret_cast<uint32_t *>(w.dmem + kOffCounter), nullptr, 0, w.st,
+                               reinterpret_cast<uint32_t *>(w.dmem)) == cudaSuccess &&
              cudaStreamSynchronize(w.st) == cudaSuccess;
         if (!ok) break;
     }
@@ -606,7 +612,7 @@ hd_status hd_server_get_stats(hd_server *s, hd_server_stats *stats)
     std::lock_guard<std::mutex> lk(s->mu);
     *stats = s->stats;
     stats->mean_wave_packets = s->stats.waves ? (double)s->wave_packets_sum / (double)s->stats.waves : 0.0;
-    const double hw = (double)s->stats.host_waves;
+    const double hw = (double)s->timed_waves;
     stats->mean_t_in_us = hw > 0 ? s->t_in_us / hw : 0.0;
     stats->mean_t_decode_us = hw > 0 ? s->t_dec_us / hw : 0.0;
     stats->mean_t_out_us = hw > 0 ? s->t_out_us / hw : 0.0;

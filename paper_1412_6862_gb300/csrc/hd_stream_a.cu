@@ -45,6 +45,8 @@ void register_stream_a(std::vector<StreamVariant> &v)
     add_variants<31, 96, 3, 32, 1>(v);
     add_variants<31, 96, 4, 32, 1>(v);
     add_variants<31, 64, 3, 32, 1>(v);
+    add_variants<31, 128, 2, 32, 1>(v);  // 32 KB per CTA: 7 CTAs, 28 warps per SM
+    add_variants<31, 64, 2, 32, 1>(v);
 }
 
 }  // namespace hd
