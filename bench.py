@@ -767,7 +767,8 @@ def run_serving(dev, args, pool=None, host=False):
         sustained = decoded / st["duration_s"] / 1e9 if st["duration_s"] > 0 else None
         offered = decoded / float(arr[-1]) / 1e9
         row = {"p50_latency_us": st["p50_latency_us"], "p99_latency_us": st["p99_latency_us"],
-               "max_latency_us": st["max_latency_us"], "sustained_gbps": sustained, "offered_gbps": offered,
+               "p999_latency_us": st["p999_latency_us"], "max_latency_us": st["max_latency_us"],
+               "max_submit_lag_us": st["max_submit_lag_us"], "sustained_gbps": sustained, "offered_gbps": offered,
                "duration_s": st["duration_s"], "waves": st["waves"], "mean_wave_packets": st["mean_wave_packets"],
                "max_resident_gb": st["max_resident_bytes"] / 1e9, "backpressure_waits": st["backpressure_waits"],
                "failed_packets": bad}

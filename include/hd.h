@@ -170,12 +170,37 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
 hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
                           void *cuda_stream);
 
-/* Segments with k >= 64 are decoded by a tiled kernel compiled in several
- * configurations (warps per CTA, pipeline stages, stage bytes).  The first
- * call for a length n on a device builds that length's output-word table
- * (cudaMalloc plus a synchronous copy of about 2 * (k + 2200) bytes; up to 32
- * lengths are kept per device, the least recently used one is freed after a
- * device synchronisation), so make it before capturing a stream.
+/* Segments with k >= 64 are decoded by a tiled kernel that reads a per-length
+ * output-word table (about 2 * (k + 2200) bytes of device memory).
+ * hd_decode_short() keeps these tables in a per-device cache: the first call
+ * for a length n builds its table (cudaMalloc plus a synchronous copy); up to
+ * 32 lengths are kept per device, and evicting the least recently used one
+ * waits only for that table's last use (an event on the stream that used it).
+ * A call on a capturing stream for a length not in the cache returns
+ * HD_ERR_INVALID_ARG and enqueues nothing, and a table used inside a capture
+ * is never evicted.  The allocation-free path is a plan: */
+typedef struct hd_short_plan hd_short_plan;
+
+/* Build the tables for segments of length n (3..32767) on the current device:
+ * the library's only allocation for that length (synchronous).  The plan is
+ * owned by the caller and freed by hd_short_plan_destroy(). */
+hd_status hd_short_plan_create(uint32_t n, hd_short_plan **plan);
+
+/* hd_decode_short() for the plan's length: arguments, results and errors as
+ * there (in_bits must equal n * num_codewords), HD_ERR_INVALID_ARG when the
+ * current device is not the plan's.  Enqueues the counters' clears and the
+ * decode on `cuda_stream` and nothing else: no allocation, no
+ * synchronisation, so it can run inside a stream capture. */
+hd_status hd_decode_short_plan(const hd_short_plan *plan, const uint32_t *stream, uint64_t in_bits,
+                               uint64_t num_codewords, uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                               unsigned long long *err_count, unsigned long long *detected_count,
+                               void *cuda_stream);
+
+/* Free a plan's tables (after the work that reads them has finished). */
+void hd_short_plan_destroy(hd_short_plan *plan);
+
+/* The tiled kernel is compiled in several configurations (warps per CTA,
+ * pipeline stages, stage bytes).
  * hd_short_variant_select() pins one configuration for every length on the
  * current device (ordinal < 0 removes the pin); hd_short_autotune() times
  * every configuration on `num_codewords` all-zero segments of length n (reps
@@ -448,6 +473,9 @@ typedef struct {
        CUDA events on the slot's stream: gather (T_PS), batched decode (T_DKE), scatter (T_PR) */
     uint64_t host_waves;
     double mean_t_in_us, mean_t_decode_us, mean_t_out_us;
+    /* filled by the trace replays: the 99.9th latency percentile, and the largest delay between a
+       packet's scheduled arrival and its submission (the replaying thread's own lateness) */
+    double p999_latency_us, max_submit_lag_us;
 } hd_server_stats;
 
 /* Create a server on the current device (allocates its slots: per slot a

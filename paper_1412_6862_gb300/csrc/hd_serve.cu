@@ -466,9 +466,16 @@ hd_status serve_trace(const hd_server_config *cfg, const hd_packet *pkts, const 
         std::nth_element(lat.begin(), lat.begin() + (long)i, lat.end());
         return lat[i];
     };
+    // how late the generator itself submitted (a sleeping thread woken late by
+    // the operating system), to tell such delays from the server's
+    double lag = 0.0;
+    for (uint32_t j = 0; j < num; ++j)
+        lag = std::max(lag, (double)((int64_t)completions[j].t_submit_ns - (int64_t)scheduled[j]) * 1e-3);
+    stats->max_submit_lag_us = lag;
+    stats->max_latency_us = num ? *std::max_element(lat.begin(), lat.end()) : 0.0;
     stats->p50_latency_us = pct(0.50);
     stats->p99_latency_us = pct(0.99);
-    stats->max_latency_us = num ? *std::max_element(lat.begin(), lat.end()) : 0.0;
+    stats->p999_latency_us = pct(0.999);
     stats->duration_s = num ? (double)(last - first) * 1e-9 : 0.0;
     stats->backpressure_waits = backpressure;
     return HD_OK;

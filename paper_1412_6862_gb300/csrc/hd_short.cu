@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <new>
 #include <type_traits>
 #include <vector>
 
@@ -698,36 +699,10 @@ std::vector<uint32_t> output_table(uint32_t n, uint32_t k, uint32_t max_tile_wor
 // entries, half the table).
 bool split_in_pass3(uint32_t k) { return k < 1280; }
 
-struct TableEntry {
-    uint32_t n = 0;
-    void *dev = nullptr;
-    uint32_t len = 0;
-    uint64_t used = 0;
-};
-constexpr int kMaxTables = 32;
-TableEntry g_tables[64][kMaxTables];
-uint64_t g_table_clock = 0;
-
-// The output-word table of length n on the current device, built on first use.
-const void *table_for(uint32_t n, uint32_t k, uint32_t *len)
+// Build the output-word table of length n on the current device: cudaMalloc
+// and a synchronous copy (the only allocation of the shortened-code path).
+cudaError_t build_short_table(uint32_t n, uint32_t k, void **dev, uint32_t *len)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(g_short_mu);
-    TableEntry *slot = nullptr;
-    for (TableEntry &e : g_tables[dev]) {
-        if (e.n == n && e.dev) {
-            e.used = ++g_table_clock;
-            *len = e.len;
-            return e.dev;
-        }
-        if (!slot || (!e.dev && slot->dev) || (e.dev && slot->dev && e.used < slot->used)) slot = &e;
-    }
-    if (slot->dev) {  // evict the least recently used table once no kernel can still read it
-        if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
-        cudaFree(slot->dev);
-        slot->dev = nullptr;
-    }
     // the longest tile of any configuration: the largest stage's codewords, plus a partial word
     const uint32_t max_words = (uint32_t)(((uint64_t)tile_codewords<8192>(n) * k + 31) / 32) + 1;
     const std::vector<uint32_t> full = output_table(n, k, max_words);
@@ -738,21 +713,98 @@ const void *table_for(uint32_t n, uint32_t k, uint32_t *len)
     const size_t bytes = wide ? full.size() * 4 : narrow.size() * 2;
     const void *src = wide ? static_cast<const void *>(full.data()) : static_cast<const void *>(narrow.data());
     void *d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
         cudaFree(d);
-        return nullptr;
+        return e;
+    }
+    *dev = d;
+    *len = (uint32_t)full.size();
+    return cudaSuccess;
+}
+
+// The tables that hd_decode_short builds on first use of a length, per
+// device, least recently used first out.  Each table's last use is an event on
+// the stream that used it, so evicting a table waits for that use only; a
+// table used while its stream was capturing may be read by any later replay
+// of that graph and is never evicted.
+struct TableEntry {
+    uint32_t n = 0;
+    void *dev = nullptr;
+    uint32_t len = 0;
+    uint64_t used = 0;
+    cudaEvent_t last = nullptr;  // recorded after each uncaptured use
+    bool pinned = false;         // used inside a stream capture
+};
+constexpr int kMaxTables = 32;
+TableEntry g_tables[64][kMaxTables];
+uint64_t g_table_clock = 0;
+
+bool stream_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// The cached table of length n for a launch on `st` (built on a miss, which a
+// capturing stream may not do: cudaErrorStreamCaptureUnsupported).
+cudaError_t table_for(uint32_t n, uint32_t k, cudaStream_t st, TableEntry **entry)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const bool capturing = stream_capturing(st);
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    TableEntry *slot = nullptr;
+    for (TableEntry &e : g_tables[dev]) {
+        if (e.n == n && e.dev) {
+            e.used = ++g_table_clock;
+            *entry = &e;
+            return cudaSuccess;
+        }
+        if (e.pinned) continue;
+        if (!slot || (!e.dev && slot->dev) || (e.dev && slot->dev && e.used < slot->used)) slot = &e;
+    }
+    if (capturing) return cudaErrorStreamCaptureUnsupported;
+    if (!slot) return cudaErrorMemoryAllocation;  // every slot is held by a captured graph
+    if (slot->dev) {  // evict once its last use has finished
+        if (slot->last && cudaEventSynchronize(slot->last) != cudaSuccess) return cudaErrorUnknown;
+        cudaFree(slot->dev);
+        slot->dev = nullptr;
+        slot->n = 0;
+    }
+    void *d = nullptr;
+    uint32_t len = 0;
+    cudaError_t e = build_short_table(n, k, &d, &len);
+    if (e != cudaSuccess) return e;
+    if (!slot->last && cudaEventCreateWithFlags(&slot->last, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(d);
+        return cudaErrorUnknown;
     }
     slot->n = n;
     slot->dev = d;
-    slot->len = (uint32_t)full.size();
+    slot->len = len;
     slot->used = ++g_table_clock;
-    *len = slot->len;
-    return d;
+    *entry = slot;
+    return cudaSuccess;
+}
+
+// Mark a cached table's use by a launch just enqueued on `st`.
+void table_used(TableEntry *e, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_short_mu);
+    if (stream_capturing(st)) e->pinned = true;
+    else cudaEventRecord(e->last, st);
 }
 
 cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
-                               int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st)
+                               int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
+                               const void *table, uint32_t tab_len)
 {
     const ShortVariant &v = kShortVariants[vi];
     const uint32_t r = short_r(n), k = n - r;
@@ -780,8 +832,9 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     const uint32_t lastbits = n + 1 - 32 * (a.Y - 1);
     a.ylast = lastbits >= 32 ? 0xFFFFFFFFu : (1u << lastbits) - 1u;
     a.tlog = team_log(a.Y, a.g);
-    a.table = table_for(n, k, &a.tab_len);
-    if (!a.table) return cudaErrorMemoryAllocation;
+    a.table = table;
+    a.tab_len = tab_len;
+    if (!a.table) return cudaErrorInvalidValue;
     a.syn_type = syn ? syn_type : 0;
     a.nJ = 0;
     for (uint32_t J = 5; (2u << J) - J - 2u < k; ++J) ++a.nJ;
@@ -835,9 +888,12 @@ hd_status hd_segment_params(uint32_t packet_bytes, uint32_t t, uint32_t *n, uint
     return HD_OK;
 }
 
-hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
-                          uint32_t *out_bits, void *syndromes, hd_syn_type syn_type, unsigned long long *err_count,
-                          unsigned long long *detected_count, void *cuda_stream)
+}  // extern "C"
+
+namespace {
+
+hd_status check_short_args(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                           uint32_t *out_bits, void *syndromes, hd_syn_type syn_type)
 {
     if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
     if (syn_type != HD_SYN_NONE && syn_type != HD_SYN_U8 && syn_type != HD_SYN_U16) return HD_ERR_INVALID_ARG;
@@ -849,18 +905,22 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
         if (syn_type != HD_SYN_NONE && !syndromes) return HD_ERR_NULL;
         if (!aligned16(stream) || !aligned16(out_bits) || (syndromes && !aligned16(syndromes))) return HD_ERR_ALIGN;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
-    if (detected_count && cudaMemsetAsync(detected_count, 0, sizeof(*detected_count), st) != cudaSuccess)
-        return HD_ERR_CUDA;
-    if (num_codewords == 0) return HD_OK;
+    return HD_OK;
+}
+
+// The decode itself, given the output-word table of n (unused for k < 64).
+hd_status decode_short_with(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                            uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                            unsigned long long *err_count, unsigned long long *detected_count, cudaStream_t st,
+                            const void *table, uint32_t tab_len)
+{
     const uint32_t r = short_r(n), k = n - r;
     const int syn = syndromes ? (int)syn_type : 0;
     if (k >= kLongMinK) {
         int vi = current_short_variant(n);
         if (kShortVariants[vi].SB * 8u < n + 256u) vi = 1;  // stage too small for one codeword: largest stage
         if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
-                               st) != cudaSuccess)
+                               st, table, tab_len) != cudaSuccess)
             return HD_ERR_CUDA;
         return HD_OK;
     }
@@ -871,6 +931,98 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
         syndromes, syn, err_count, detected_count);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status clear_counts(unsigned long long *err_count, unsigned long long *detected_count, cudaStream_t st)
+{
+    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
+    if (detected_count && cudaMemsetAsync(detected_count, 0, sizeof(*detected_count), st) != cudaSuccess)
+        return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+}  // namespace
+
+struct hd_short_plan {
+    int device = 0;
+    uint32_t n = 0;
+    void *table = nullptr;  // output-word table (k >= 64), owned by the plan
+    uint32_t tab_len = 0;
+};
+
+extern "C" {
+
+hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
+                          uint32_t *out_bits, void *syndromes, hd_syn_type syn_type, unsigned long long *err_count,
+                          unsigned long long *detected_count, void *cuda_stream)
+{
+    hd_status rc = check_short_args(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type);
+    if (rc != HD_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const uint32_t k = n - short_r(n);
+    TableEntry *e = nullptr;
+    if (num_codewords != 0 && k >= kLongMinK) {
+        const cudaError_t te = table_for(n, k, st, &e);
+        if (te == cudaErrorStreamCaptureUnsupported) return HD_ERR_INVALID_ARG;  // build it outside the capture
+        if (te != cudaSuccess) return HD_ERR_CUDA;
+    }
+    if ((rc = clear_counts(err_count, detected_count, st)) != HD_OK) return rc;
+    if (num_codewords == 0) return HD_OK;
+    rc = decode_short_with(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
+                           detected_count, st, e ? e->dev : nullptr, e ? e->len : 0);
+    if (e && rc == HD_OK) table_used(e, st);
+    return rc;
+}
+
+hd_status hd_short_plan_create(uint32_t n, hd_short_plan **plan)
+{
+    if (!plan) return HD_ERR_NULL;
+    *plan = nullptr;
+    if (n < 3 || n > kShortMaxN) return HD_ERR_INVALID_N;
+    hd_short_plan *p = new (std::nothrow) hd_short_plan();
+    if (!p) return HD_ERR_CAPACITY;
+    p->n = n;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return HD_ERR_CUDA;
+    }
+    const uint32_t k = n - short_r(n);
+    if (k >= kLongMinK && build_short_table(n, k, &p->table, &p->tab_len) != cudaSuccess) {
+        delete p;
+        return HD_ERR_CUDA;
+    }
+    *plan = p;
+    return HD_OK;
+}
+
+hd_status hd_decode_short_plan(const hd_short_plan *plan, const uint32_t *stream, uint64_t in_bits,
+                               uint64_t num_codewords, uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
+                               unsigned long long *err_count, unsigned long long *detected_count, void *cuda_stream)
+{
+    if (!plan) return HD_ERR_NULL;
+    hd_status rc = check_short_args(stream, in_bits, plan->n, num_codewords, out_bits, syndromes, syn_type);
+    if (rc != HD_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HD_ERR_CUDA;
+    if (dev != plan->device) return HD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if ((rc = clear_counts(err_count, detected_count, st)) != HD_OK) return rc;
+    if (num_codewords == 0) return HD_OK;
+    return decode_short_with(stream, in_bits, plan->n, num_codewords, out_bits, syndromes, syn_type, err_count,
+                             detected_count, st, plan->table, plan->tab_len);
+}
+
+void hd_short_plan_destroy(hd_short_plan *plan)
+{
+    if (!plan) return;
+    if (plan->table) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != plan->device) cudaSetDevice(plan->device);
+        cudaFree(plan->table);  // waits for the work that may still read it
+        if (cur != plan->device) cudaSetDevice(cur);
+    }
+    delete plan;
 }
 
 hd_status hd_encode_short(const uint32_t *data_bits, uint32_t n, uint64_t num_codewords, uint32_t *stream,
@@ -915,11 +1067,14 @@ hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, v
     // all-zero segments are codewords: the timing sees the common no-error path
     if (rc == HD_OK && cudaMemsetAsync(din, 0, in_b, st) != cudaSuccess) rc = HD_ERR_CUDA;
     auto *cnt = static_cast<unsigned long long *>(dcnt);
+    TableEntry *tab = nullptr;
+    if (rc == HD_OK && table_for(n, k, st, &tab) != cudaSuccess) rc = HD_ERR_CUDA;
     for (int v = 0; rc == HD_OK && v < kNumShortVariants; ++v) {
         if (kShortVariants[v].SB * 8u < n + 256u) continue;
         auto go = [&]() {
             return launch_short_tiles(v, static_cast<const uint32_t *>(din), n, num_codewords,
-                                      static_cast<uint32_t *>(dout), dsyn, HD_SYN_U16, cnt, cnt + 1, st);
+                                      static_cast<uint32_t *>(dout), dsyn, HD_SYN_U16, cnt, cnt + 1, st, tab->dev,
+                                      tab->len);
         };
         if (go() != cudaSuccess) {  // warm-up (also configures the kernel)
             rc = HD_ERR_CUDA;
@@ -938,6 +1093,7 @@ hd_status hd_short_autotune(uint32_t n, uint64_t num_codewords, uint32_t reps, v
             best_ms = ms;
         }
     }
+    if (tab) table_used(tab, st);
     if (din) cudaFree(din);
     if (dout) cudaFree(dout);
     if (dsyn) cudaFree(dsyn);

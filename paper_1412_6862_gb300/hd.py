@@ -88,7 +88,8 @@ class ServerStats(ctypes.Structure):
                 ("max_resident_bytes", _u64), ("mean_wave_packets", _c.c_double), ("p50_latency_us", _c.c_double),
                 ("p99_latency_us", _c.c_double), ("max_latency_us", _c.c_double), ("duration_s", _c.c_double),
                 ("backpressure_waits", _u64), ("host_waves", _u64), ("mean_t_in_us", _c.c_double),
-                ("mean_t_decode_us", _c.c_double), ("mean_t_out_us", _c.c_double)]
+                ("mean_t_decode_us", _c.c_double), ("mean_t_out_us", _c.c_double),
+                ("p999_latency_us", _c.c_double), ("max_submit_lag_us", _c.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -132,6 +133,9 @@ SIGNATURES = {
     "hd_segment_params": (_i32, [_u32, _u32, _c.POINTER(_u32), _c.POINTER(_u32), _c.POINTER(_u32)]),
     "hd_decode_short": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp, _vp]),
     "hd_encode_short": (_i32, [_vp, _u32, _u64, _vp, _vp]),
+    "hd_short_plan_create": (_i32, [_u32, _c.POINTER(_vp)]),
+    "hd_decode_short_plan": (_i32, [_vp, _vp, _u64, _u64, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "hd_short_plan_destroy": (None, [_vp]),
     "hd_short_variant_count": (_i32, [_c.POINTER(_u32)]),
     "hd_short_variant_select": (_i32, [_c.c_int32]),
     "hd_short_autotune": (_i32, [_u32, _u64, _u32, _vp, _c.POINTER(_c.c_int32)]),
@@ -580,6 +584,46 @@ def decode_short(stream_words, n: int, num_codewords: int, syn_type: int = SYN_U
                          _ptr(counts) + 8, _stream_handle(cuda_stream))
     check(rc, "hd_decode_short")
     return out, syndromes, counts
+
+
+class ShortPlan:
+    """The tables of one shortened-code length (hd_short_plan_*): decodes with
+    it allocate nothing and may run inside a stream capture."""
+
+    def __init__(self, n: int):
+        h = _vp()
+        check(lib().hd_short_plan_create(n, ctypes.byref(h)), "hd_short_plan_create")
+        self.handle, self.n = h.value, n
+
+    def decode(self, stream_words, num_codewords: int, syn_type: int = SYN_U16, out=None, syndromes=None,
+               counts=None, cuda_stream=None):
+        """As decode_short(); returns (out_words, syndromes or None, counts)."""
+        import torch
+        r, k = hd_short_params(self.n)
+        dev = stream_words.device
+        if out is None:
+            out = torch.empty(max(4, words_for(num_codewords * k)), dtype=torch.int32, device=dev)
+        if syndromes is None and syn_type != SYN_NONE:
+            dt = torch.uint8 if syn_type == SYN_U8 else torch.int16
+            syndromes = torch.empty(max(16, num_codewords), dtype=dt, device=dev)
+        if counts is None:
+            counts = torch.empty(2, dtype=torch.int64, device=dev)
+        rc = lib().hd_decode_short_plan(self.handle, _ptr(stream_words), self.n * num_codewords, num_codewords,
+                                        _ptr(out), _ptr(syndromes) if syn_type != SYN_NONE else None, syn_type,
+                                        _ptr(counts), _ptr(counts) + 8, _stream_handle(cuda_stream))
+        check(rc, "hd_decode_short_plan")
+        return out, syndromes, counts
+
+    def close(self) -> None:
+        if self.handle:
+            lib().hd_short_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def encode_short(data_words, n: int, num_codewords: int, out=None, cuda_stream=None):

@@ -205,3 +205,63 @@ def test_autotune_keeps_parity():
         assert hd.hd_short_autotune(33, 1000, 1) == -1  # k < 64: a single kernel
     finally:
         hd.hd_short_variant_select(-1)
+
+
+@pytest.mark.parametrize("n", [33, 545, 2679, 32767])
+def test_plan_matches_oracle_and_runs_inside_a_capture(n):
+    """hd_decode_short_plan: bit-exact against the oracle, directly and when
+    recorded in a CUDA graph and replayed (the plan allocates nothing and
+    synchronises nothing, so the decode can be captured)."""
+    import torch
+    r, k = oracle.short_params(n)
+    N = 4001 if n < 10000 else 77
+    rx, _, _ = _received(n, N, seed=n + 61, p1=0.3, p2=0.2)
+    eo, es, ee, ed = oracle.decode_short(rx, n, N, oracle.SYN_U16, threads=8)
+    d_in = gc.to_device(rx, pad_words=4)
+    nw = hd.words_for(N * k)
+    plan = hd.ShortPlan(n)
+    try:
+        def check(out, syn, counts):
+            assert np.array_equal(gc.host_u32(out)[:nw], eo[:nw])
+            assert np.array_equal(syn.cpu().numpy()[:N].view(np.uint16), es[:N])
+            assert tuple(int(x) for x in counts.cpu().numpy()) == (ee, ed)
+
+        out, syn, counts = plan.decode(d_in, N, hd.SYN_U16)
+        torch.cuda.synchronize()
+        check(out, syn, counts)
+        out.fill_(-1)
+        syn.fill_(0x55)
+        counts.fill_(9)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.decode(d_in, N, hd.SYN_U16, out=out, syndromes=syn, counts=counts, cuda_stream=s)
+        for _ in range(2):
+            out.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            check(out, syn, counts)
+    finally:
+        plan.close()
+    assert hd.hd_device_status() == 0
+
+
+def test_cached_path_refuses_a_new_length_inside_a_capture():
+    """hd_decode_short builds a length's table on first use, which cannot
+    happen inside a stream capture: the call is refused and nothing is
+    enqueued (the capture stays valid)."""
+    import torch
+    n = 4093  # a length no other test decodes
+    r, k = oracle.short_params(n)
+    N = 64
+    rx, _, _ = _received(n, N, seed=3)
+    d_in = gc.to_device(rx, pad_words=4)
+    out = torch.empty(hd.words_for(N * k) + 4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = hd.hd_decode_short(d_in.data_ptr(), n * N, n, N, out.data_ptr(), None, hd.SYN_NONE, None, None,
+                                s.cuda_stream)
+    assert rc == hd.HD_ERR_INVALID_ARG
+    del g
+    _check(n, N, hd.SYN_U16, seed=3)  # outside a capture the same length decodes
