@@ -745,16 +745,20 @@ def run_serving(dev, args, pool=None, host=False):
     bits = [N * code_params(n)[1] for (n, N, *_r) in layout]
     num = args.serve_packets
     table = hd.packet_table([rows[j % P] for j in range(num)])
-    staging = (256 << 20) if host else 0
-    cfg = hd.server_config(max_waves=4, max_wave_packets=4096, max_wave_tiles=1 << 16,
+    # host waves also copy their packets in and out: fewer packets per wave
+    # keep one wave's copies short (a wave takes whatever is waiting)
+    staging = (64 << 20) if host else 0
+    wave_packets = 512 if host else 4096
+    cfg = hd.server_config(max_waves=4, max_wave_packets=wave_packets, max_wave_tiles=1 << 16,
                            queue_capacity=max(1 << 16, num), mem_cap_bytes=4 << 30, host_staging_bytes=staging)
     setup_s = time.perf_counter() - t_setup
     src = "pinned host memory (gather, decode and scatter per wave on the slot's stream)" if host else \
         "a device pool (arrival = descriptor enqueue)"
     out = {"workload": f"open-loop Poisson arrivals of packets from the batched distribution ({P}-packet pool in "
-                       f"{src}, cycled), {num} packets per rate; continuous batching with 4 wave slots, <= 4096 "
-                       f"packets per wave, 4 GB admission budget; latency = scheduled arrival -> completion seen "
-                       f"by the host", "setup_s": setup_s, "rates": {}}
+                       f"{src}, cycled), {num} packets per rate; continuous batching with 4 wave slots, <= "
+                       f"{wave_packets} packets per wave{', 64 MB of staging per slot' if host else ''}, 4 GB "
+                       f"admission budget; latency = scheduled arrival -> completion seen by the host",
+           "setup_s": setup_s, "rates": {}}
     base, extra = serve_rates(args)
     best, saturated_at = 0.0, None
     for i, rate in enumerate(base + extra):

@@ -328,11 +328,17 @@ typedef struct {
  * A plan is not thread-safe: launch it from one host thread at a time. */
 typedef struct hd_plan hd_plan;
 
+/* A plan decodes with one of num_variants configurations: variants
+ * 0 .. num_variants - 2 launch one persistent kernel that decodes tiles of
+ * every n; the last one (the split configuration) launches one kernel per
+ * code length present, each compiled for that n alone, as concurrent branches
+ * forked from and joined back into the launching stream (its n = 15 kernel
+ * holds the n = 15 decode table once that is filled). */
 typedef struct {
     uint32_t num_packets;
     uint32_t num_tiles;     /* warp work items: full chunks plus ragged tails */
     uint32_t full_tiles;
-    uint32_t warps_per_cta; /* batch-kernel configuration in use */
+    uint32_t warps_per_cta; /* batch-kernel configuration in use (split: that of the kernels without a table) */
     uint32_t stages;
     uint32_t smem_bytes;
     uint32_t variant;       /* index of the configuration, < num_variants */

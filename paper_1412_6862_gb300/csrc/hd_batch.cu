@@ -197,8 +197,10 @@ __device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return (uint32
 
 // lut7 (or nullptr: arithmetic decode) and, with T15, lut15 (required) are
 // the global decode tables of n = 7 and 15; the kernel copies them into shared
-// memory once per CTA.
-template <int WARPS, int S, bool T15>
+// memory once per CTA.  NSEL = 0 decodes tiles of every n; NSEL = n compiles
+// only the decoder of that n (every tile of the table must be of that n), so
+// that the kernel's code fits the instruction cache.
+template <int WARPS, int S, bool T15, int NSEL = 0>
 __global__ void __launch_bounds__(WARPS * 32)
     k_decode_batch(const DevTile *__restrict__ tiles, uint32_t num_tiles, uint32_t *__restrict__ counter,
                    unsigned long long *__restrict__ err_counts, uint32_t *__restrict__ status,
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 bulk_g2s(smem + Cfg::off_lut15 + o, reinterpret_cast<const uint8_t *>(lut15) + o, 16384u, lut_bar);
         }
     }
-    if (lut7 != nullptr && threadIdx.x < 16)  // 256 bytes
+    if ((NSEL == 0 || NSEL == 7) && lut7 != nullptr && threadIdx.x < 16)  // 256 bytes
         reinterpret_cast<uint4 *>(smem + Cfg::off_lut7)[threadIdx.x] =
             __ldg(reinterpret_cast<const uint4 *>(lut7) + threadIdx.x);
     __syncthreads();  // the n = 7 table is in place and the table barrier initialised
@@ -299,7 +301,8 @@ __global__ void __launch_bounds__(WARPS * 32)
         uint8_t *sbuf = s_syn;
         uint8_t *sdst = (full && p.syn_type != 0) ? p.syn + tl.c0 * (p.syn_type == 2 ? 2u : 1u) : sbuf;
         unsigned long long errs = 0;
-        if (full || p.n != 3) {
+        const bool chunked = NSEL == 0 ? (full || p.n != 3) : NSEL != 3;  // n = 3 tiles are all tails
+        if (chunked) {
             const uint32_t cwords = chunk_codewords(p.n);
             const uint32_t k = p.n - p.m;
             const uint32_t cnt = tl.count & ~kFullTile;
@@ -322,22 +325,34 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
             uint32_t e = 0;
             const uint32_t nch = full ? chunks : 1u;
-            switch (p.n) {
-                case 7:
-                    e = lut7 != nullptr ? batch_chunk_syn<7, true>(p.syn_type, stage, sdst, lane, nch, s_lut7)
-                                        : batch_chunk_syn<7>(p.syn_type, stage, sdst, lane, nch);
-                    break;
-                case 15:
-                    if constexpr (T15)
-                        e = batch_chunk_syn<15, true>(p.syn_type, stage, sdst, lane, nch, s_lut15);
-                    else
-                        e = batch_chunk_syn<15>(p.syn_type, stage, sdst, lane, nch);
-                    break;
-                case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sdst, lane, nch); break;
-                case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sdst, lane, nch); break;
-                case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sdst, lane, nch); break;
-                case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sdst, lane, nch); break;
-                default: break;  // the plan never makes chunk tiles of other lengths
+            if constexpr (NSEL == 0) {
+                switch (p.n) {
+                    case 7:
+                        e = lut7 != nullptr ? batch_chunk_syn<7, true>(p.syn_type, stage, sdst, lane, nch, s_lut7)
+                                            : batch_chunk_syn<7>(p.syn_type, stage, sdst, lane, nch);
+                        break;
+                    case 15:
+                        if constexpr (T15)
+                            e = batch_chunk_syn<15, true>(p.syn_type, stage, sdst, lane, nch, s_lut15);
+                        else
+                            e = batch_chunk_syn<15>(p.syn_type, stage, sdst, lane, nch);
+                        break;
+                    case 31: e = batch_chunk_syn<31>(p.syn_type, stage, sdst, lane, nch); break;
+                    case 63: e = batch_chunk_syn<63>(p.syn_type, stage, sdst, lane, nch); break;
+                    case 127: e = batch_chunk_syn<127>(p.syn_type, stage, sdst, lane, nch); break;
+                    case 255: e = batch_chunk_syn<255>(p.syn_type, stage, sdst, lane, nch); break;
+                    default: break;  // the plan never makes chunk tiles of other lengths
+                }
+            } else if constexpr (NSEL == 7) {
+                e = lut7 != nullptr ? batch_chunk_syn<7, true>(p.syn_type, stage, sdst, lane, nch, s_lut7)
+                                    : batch_chunk_syn<7>(p.syn_type, stage, sdst, lane, nch);
+            } else if constexpr (NSEL == 15) {
+                if constexpr (T15)
+                    e = batch_chunk_syn<15, true>(p.syn_type, stage, sdst, lane, nch, s_lut15);
+                else
+                    e = batch_chunk_syn<15>(p.syn_type, stage, sdst, lane, nch);
+            } else if constexpr (NSEL != 3) {
+                e = batch_chunk_syn<NSEL>(p.syn_type, stage, sdst, lane, nch);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
@@ -407,15 +422,16 @@ struct BatchVariant {
                    unsigned long long *, uint32_t *, const uint16_t *, const uint16_t *);
 };
 
-template <int W, int S, bool T15>
+template <int W, int S, bool T15, int NSEL = 0>
 void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevTile *tiles, uint32_t num_tiles,
                          uint32_t *counter, unsigned long long *err, uint32_t *status, const uint16_t *lut7,
                          const uint16_t *lut15)
 {
-    k_decode_batch<W, S, T15><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status, lut7, lut15);
+    k_decode_batch<W, S, T15, NSEL><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status, lut7,
+                                                                 lut15);
 }
 
-template <int W, int S, bool T15 = false>
+template <int W, int S, bool T15 = false, int NSEL = 0>
 BatchVariant make_batch_variant()
 {
     BatchVariant v;
@@ -423,9 +439,38 @@ BatchVariant make_batch_variant()
     v.stages = S;
     v.t15 = T15;
     v.smem = BatchCfg<W, S, T15>::smem;
-    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S, T15>);
-    v.launch = &launch_batch_kernel<W, S, T15>;
+    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S, T15, NSEL>);
+    v.launch = &launch_batch_kernel<W, S, T15, NSEL>;
     return v;
+}
+
+// The split configuration: one kernel per code length, each compiled for its
+// n only, launched as concurrent branches of the plan's graph.  Index i
+// follows kSplitOrder; n = 15 has a second kernel that holds its decode table
+// (used when the table is filled).
+constexpr uint32_t kSplitOrder[] = {255, 127, 63, 31, 15, 7, 3};
+constexpr int kSplitGroups = 7;
+
+struct SplitKernels {
+    BatchVariant group[kSplitGroups];
+    BatchVariant n15_table;
+};
+
+const SplitKernels &split_kernels()
+{
+    static const SplitKernels k = [] {
+        SplitKernels s;
+        s.group[0] = make_batch_variant<1, 3, false, 255>();
+        s.group[1] = make_batch_variant<1, 3, false, 127>();
+        s.group[2] = make_batch_variant<1, 3, false, 63>();
+        s.group[3] = make_batch_variant<1, 3, false, 31>();
+        s.group[4] = make_batch_variant<1, 3, false, 15>();
+        s.group[5] = make_batch_variant<1, 3, false, 7>();
+        s.group[6] = make_batch_variant<1, 3, false, 3>();
+        s.n15_table = make_batch_variant<12, 2, true, 15>();
+        return s;
+    }();
+    return k;
 }
 
 static const std::vector<BatchVariant> &batch_variants()
@@ -460,6 +505,12 @@ struct hd_plan {
     cudaGraphExec_t exec = nullptr;
     unsigned long long *graph_err = nullptr;
     bool graph_ok = false;
+    uint64_t graph_kernels = 0;  // kernels one replay of the graph launches
+    // the split configuration: each code group's tile range (tiles are grouped
+    // by n in kSplitOrder), a stream per group and the fork/join events
+    uint32_t grp_begin[kSplitGroups] = {}, grp_end[kSplitGroups] = {};
+    cudaStream_t gstream[kSplitGroups] = {};
+    cudaEvent_t fork = nullptr, join[kSplitGroups] = {};
 };
 
 namespace {
@@ -507,11 +558,11 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
     tiles.clear();
     tiles.reserve(ntiles);
     // tiles grouped by n (long codes first), each code's tails among its full tiles
-    static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
     uint32_t nfull_tiles = 0;
-    for (uint32_t n : order)
+    for (int gi = 0; gi < kSplitGroups; ++gi) {
+        if (stats) stats->grp_begin[gi] = (uint32_t)tiles.size();
         emit_code_tiles(
-            n, num_packets,
+            kSplitOrder[gi], num_packets,
             [&](uint32_t i) {
                 const DevPacket &d = pk[i];
                 return PacketView{d.in, d.out, d.syn, d.num_cw, d.n, d.m, d.syn_type};
@@ -520,6 +571,8 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
                 tiles.push_back(t);
                 if (t.count & kFullTile) ++nfull_tiles;
             });
+        if (stats) stats->grp_end[gi] = (uint32_t)tiles.size();
+    }
     if (stats) stats->full_tiles = nfull_tiles;
     return HD_OK;
 }
@@ -543,7 +596,14 @@ struct LaunchGeom {
     int grid;
     uint32_t *status;
     const uint16_t *lut7, *lut15;
+    bool split = false;
+    const BatchVariant *gk[kSplitGroups] = {};  // split: the kernel of each code group
+    int ggrid[kSplitGroups] = {};
 };
+
+// Index of the split configuration among a plan's configurations (after the
+// single-kernel ones).
+inline int split_variant() { return (int)batch_variants().size(); }
 
 cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
 {
@@ -551,6 +611,21 @@ cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
     if (g->status == nullptr) return cudaErrorInvalidSymbol;
     g->variant = p->variant;
     g->lut7 = lut_ptr(7, st);
+    if (g->variant == split_variant()) {
+        g->split = true;
+        g->lut15 = lut_ptr(15, st);
+        g->grid = 0;
+        const SplitKernels &sk = split_kernels();
+        for (int gi = 0; gi < kSplitGroups; ++gi) {
+            const uint32_t nt = p->grp_end[gi] - p->grp_begin[gi];
+            if (nt == 0) continue;
+            g->gk[gi] = (kSplitOrder[gi] == 15 && g->lut15 != nullptr) ? &sk.n15_table : &sk.group[gi];
+            g->ggrid[gi] = batch_grid(*g->gk[gi], nt);
+            if (g->ggrid[gi] <= 0) return cudaErrorInvalidConfiguration;
+            g->grid += g->ggrid[gi];
+        }
+        return cudaSuccess;
+    }
     g->lut15 = batch_variants()[g->variant].t15 ? lut_ptr(15, st) : nullptr;
     if (batch_variants()[g->variant].t15 && g->lut15 == nullptr) g->variant = 0;
     g->grid = batch_grid(batch_variants()[g->variant], p->num_tiles);
@@ -560,12 +635,11 @@ cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
 cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *err_counts, cudaStream_t st,
                          bool clear = true)
 {
-    const BatchVariant &v = batch_variants()[g.variant];
-    const int grid = g.grid;
     uint32_t *status = g.status;
     cudaError_t e = cudaSuccess;
     if (clear) {
-        e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t), st);
+        // one claim counter per code group (the split configuration), else the first
+        e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t) * (g.split ? kSplitGroups : 1), st);
         if (e != cudaSuccess) return e;
         if (err_counts) {
             e = cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * p->num_packets, st);
@@ -573,8 +647,35 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
         }
     }
     if (p->num_tiles == 0) return cudaSuccess;
-    v.launch(grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15);
+    if (g.split) {
+        // the code groups as concurrent branches forked from `st` and joined back into it
+        if ((e = cudaEventRecord(p->fork, st)) != cudaSuccess) return e;
+        for (int gi = 0; gi < kSplitGroups; ++gi) {
+            if (!g.gk[gi]) continue;
+            cudaStream_t gs = p->gstream[gi];
+            if ((e = cudaStreamWaitEvent(gs, p->fork, 0)) != cudaSuccess) return e;
+            const BatchVariant &v = *g.gk[gi];
+            v.launch(g.ggrid[gi], v.smem, gs, p->d_tiles + p->grp_begin[gi], p->grp_end[gi] - p->grp_begin[gi],
+                     p->d_counter + gi, err_counts, status, g.lut7, g.lut15);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(p->join[gi], gs)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, p->join[gi], 0)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const BatchVariant &v = batch_variants()[g.variant];
+    v.launch(g.grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15);
     return cudaGetLastError();
+}
+
+// Kernels enqueued by one launch of a prepared plan.
+uint64_t plan_kernels(const hd_plan *p, const LaunchGeom &g)
+{
+    if (p->num_tiles == 0) return 0;
+    if (!g.split) return 1;
+    uint64_t c = 0;
+    for (int gi = 0; gi < kSplitGroups; ++gi) c += g.gk[gi] != nullptr;
+    return c;
 }
 
 void drop_graph(hd_plan *p)
@@ -644,11 +745,15 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     }
     p->d_tiles = static_cast<DevTile *>(p->dmem);
     p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + tl_b);
-    if ((!tiles.empty() &&
-         cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaFree(p->dmem);
-        delete p;
+    bool ok = (tiles.empty() || cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
+                                           cudaMemcpyHostToDevice) == cudaSuccess) &&
+              cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int gi = 0; ok && gi < kSplitGroups; ++gi)
+        ok = cudaStreamCreateWithFlags(&p->gstream[gi], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->join[gi], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        hd_plan_destroy(p);
         return HD_ERR_CUDA;
     }
     *out = p;
@@ -678,9 +783,10 @@ hd_status hd_plan_launch(hd_plan *p, unsigned long long *err_counts, void *cuda_
         }
         p->graph_err = err_counts;
         p->graph_ok = true;
+        p->graph_kernels = plan_kernels(p, geom);
     }
     if (cudaGraphLaunch(p->exec, st) != cudaSuccess) return HD_ERR_CUDA;
-    if (p->num_tiles) count_launch();
+    count_launch(p->graph_kernels);
     return HD_OK;
 }
 
@@ -695,8 +801,8 @@ hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan
     float best_us = 0.f;
     const int keep = p->variant;
     hd_status rc = HD_OK;
-    for (size_t i = 0; i < batch_variants().size(); ++i) {
-        p->variant = (int)i;
+    for (int i = 0; i <= split_variant(); ++i) {
+        p->variant = i;
         LaunchGeom geom;
         if (prepare_plan(p, &geom, st) != cudaSuccess || geom.variant != (int)i) continue;
         if (enqueue_plan(p, geom, nullptr, st) != cudaSuccess) {
@@ -714,7 +820,7 @@ hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan
         cudaEventElapsedTime(&ms, e0, e1);
         const float us = ms * 1000.f / (float)reps;
         if (best < 0 || us < best_us) {
-            best = (int)i;
+            best = i;
             best_us = us;
         }
     }
@@ -732,7 +838,8 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
 {
     if (!p || !info) return HD_ERR_NULL;
     std::memset(info, 0, sizeof(*info));
-    const BatchVariant &v = batch_variants()[p->variant];
+    const bool split = p->variant == split_variant();
+    const BatchVariant &v = split ? split_kernels().group[0] : batch_variants()[p->variant];
     info->num_packets = p->num_packets;
     info->num_tiles = p->num_tiles;
     info->full_tiles = p->full_tiles;
@@ -744,16 +851,16 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
     info->stages = (uint32_t)v.stages;
     info->smem_bytes = v.smem;
     info->variant = (uint32_t)p->variant;
-    info->num_variants = (uint32_t)batch_variants().size();
+    info->num_variants = (uint32_t)split_variant() + 1;
     info->measured_us = p->tuned_us;
-    info->table_lookup = 1u | (v.t15 ? 2u : 0u);
+    info->table_lookup = 1u | (v.t15 || split ? 2u : 0u);
     return HD_OK;
 }
 
 hd_status hd_plan_select(hd_plan *p, uint32_t variant)
 {
     if (!p) return HD_ERR_NULL;
-    if (variant >= batch_variants().size()) return HD_ERR_INVALID_ARG;
+    if (variant > (uint32_t)split_variant()) return HD_ERR_INVALID_ARG;
     p->variant = (int)variant;
     drop_graph(p);
     return HD_OK;
@@ -764,6 +871,11 @@ void hd_plan_destroy(hd_plan *p)
     if (!p) return;
     drop_graph(p);
     if (p->capture) cudaStreamDestroy(p->capture);
+    for (int gi = 0; gi < kSplitGroups; ++gi) {
+        if (p->gstream[gi]) cudaStreamDestroy(p->gstream[gi]);
+        if (p->join[gi]) cudaEventDestroy(p->join[gi]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     if (p->dmem) cudaFree(p->dmem);
     delete p;
 }

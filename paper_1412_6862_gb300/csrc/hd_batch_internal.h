@@ -81,7 +81,7 @@ struct CopyPiece {
     uint32_t pad;
 };
 
-constexpr uint32_t kPieceBytes = 32768;
+constexpr uint32_t kPieceBytes = 8192;
 
 // Cut a copy of `bytes` into pieces appended to `out`.
 inline void add_copy_pieces(std::vector<CopyPiece> &out, const void *src, void *dst, uint64_t bytes)

@@ -9,13 +9,14 @@
 namespace hd {
 namespace {
 
-constexpr int kCopyThreads = 256;
+constexpr int kCopyThreads = 128;
 constexpr int kCopyVecs = kPieceBytes / 16 / kCopyThreads;  // 16-byte vectors per thread
 static_assert(kCopyVecs * 16 * kCopyThreads == (int)kPieceBytes, "a piece is one pass of the CTA");
 
 // One CTA per piece (grid-strided): every thread issues all of its loads
 // before its first store, so a CTA keeps a whole piece in flight, which
-// hides the latency of reads from host memory.
+// hides the latency of reads from host memory; small pieces spread even a
+// wave of a few packets over many SMs.
 __global__ void __launch_bounds__(kCopyThreads) k_copy_pieces(const CopyPiece *__restrict__ pieces, uint32_t count)
 {
     for (uint32_t pi = blockIdx.x; pi < count; pi += gridDim.x) {
