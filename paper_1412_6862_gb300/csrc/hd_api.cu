@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "hd_device.cuh"
 #include "hd_internal.h"
 
 namespace hd {
@@ -32,6 +33,27 @@ int num_sms()
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+namespace {
+
+// Lets the next kernel of the stream launch at once, then clears the counters.
+__global__ void k_zero_counts(unsigned long long *a, unsigned long long *b)
+{
+    grid_dep_launch_dependents();
+    if (threadIdx.x == 0) {
+        if (a) *a = 0ull;
+        if (b) *b = 0ull;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st)
+{
+    k_zero_counts<<<1, 32, 0, st>>>(a, b);
+    count_launch();
+    return cudaGetLastError();
+}
 
 }  // namespace hd
 
@@ -96,10 +118,10 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
     const uint64_t in_words = words_for_bits(in_bits);
     const uint64_t out_words = words_for_bits(num_codewords * k);
     const int syn = syndromes ? (int)syn_type : 0;
-    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
+    if (err_count && launch_zero_counts(err_count, nullptr, st) != cudaSuccess) return HD_ERR_CUDA;
     uint64_t covered = 0;
-    if (launch_decode_fast(stream, n, num_codewords, out_bits, syndromes, syn, err_count, st, &covered) !=
-        cudaSuccess)
+    if (launch_decode_fast(stream, n, num_codewords, out_bits, syndromes, syn, err_count, st, &covered,
+                           err_count != nullptr) != cudaSuccess)
         return HD_ERR_CUDA;
     if (covered < num_codewords) {
         const uint64_t tile_begin = covered / 32, tile_end = (num_codewords + 31) / 32;

@@ -158,7 +158,7 @@ uint32_t read_clear_status_decode()
 }
 
 cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
-                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered)
+                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered, bool pdl)
 {
     *covered = 0;
     const int idx = chosen_variant(n, syn_type);
@@ -174,14 +174,14 @@ cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, 
         if (lut == nullptr) return cudaSuccess;  // no table yet (first call inside a capture): generic path
     }
     *covered = nchunks * v.chunk_cw;
-    return v.launch(v, in, nchunks, out, syn, err, status, st, nullptr, lut);
+    return v.launch(v, in, nchunks, out, syn, err, status, st, nullptr, lut, pdl);
 }
 
 // SECDED: the streaming kernel with codewords of n + 1 bits, compiled in the
 // built-in configuration of n for each syndrome type.
 cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
                                       int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
-                                      uint64_t *covered)
+                                      uint64_t *covered, bool pdl)
 {
     *covered = 0;
     // a pinned configuration (hd_secded_variant_select), else the table
@@ -215,7 +215,7 @@ cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t n
     uint32_t *status = status_ptr();
     if (status == nullptr) return cudaErrorInvalidSymbol;
     *covered = nchunks * v->chunk_cw;
-    return v->launch(*v, in, nchunks, out, syn, err, status, st, det, v->lut ? lut : nullptr);
+    return v->launch(*v, in, nchunks, out, syn, err, status, st, det, v->lut ? lut : nullptr, pdl);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,7 +434,7 @@ hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, 
         const uint16_t *lut = v.lut ? lut_ptr(n, st) : nullptr;
         if (v.lut && lut == nullptr) continue;
         if (v.launch(v, static_cast<const uint32_t *>(din[0]), nchunks, static_cast<uint32_t *>(dout[0]),
-                     syn_type == HD_SYN_NONE ? nullptr : dsyn[0], er, status, st, nullptr, lut) != cudaSuccess) {
+                     syn_type == HD_SYN_NONE ? nullptr : dsyn[0], er, status, st, nullptr, lut, false) != cudaSuccess) {
             rc = HD_ERR_CUDA;
             break;
         }
@@ -448,7 +448,7 @@ hd_status hd_autotune(uint32_t n, hd_syn_type syn_type, uint64_t num_codewords, 
             cudaEventRecord(e0, st);
             for (int i = 0; i < nsets; ++i)
                 v.launch(v, static_cast<const uint32_t *>(din[i]), c.nchunks, static_cast<uint32_t *>(dout[i]),
-                         syn_type == HD_SYN_NONE ? nullptr : dsyn[i], er, status, st, nullptr, c.lut);
+                         syn_type == HD_SYN_NONE ? nullptr : dsyn[i], er, status, st, nullptr, c.lut, false);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = HD_ERR_CUDA;

@@ -146,6 +146,19 @@ __device__ __forceinline__ void bulk_wait_all()
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Programmatic dependent launch (sm_90+).  A kernel launched with the
+// programmatic-serialisation attribute may start before the kernel ahead of
+// it in the stream has finished, once every CTA of that kernel has executed
+// launch_dependents; wait blocks the executing thread until the kernels ahead
+// have completed and their memory operations are visible.  Without such a
+// dependency wait returns at once.
+__device__ __forceinline__ void grid_dep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Orders this thread's generic-proxy shared-memory accesses before later
 // async-proxy (bulk copy) accesses to the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem()

@@ -48,17 +48,26 @@ cudaError_t launch_decode_generic(const uint32_t *in, uint64_t in_words, uint32_
 cudaError_t launch_encode_generic(const uint32_t *data, uint64_t data_words, uint32_t n, uint64_t num_cw,
                                   uint32_t *stream, uint64_t stream_words, cudaStream_t st);
 
+// Clear one or two device counters (either may be NULL) with a one-thread
+// kernel that lets the next kernel of the stream start at once (programmatic
+// dependent launch): a launch with pdl = true below overlaps it and waits for
+// it only before adding to the counters.  Inside a CUDA graph this costs far
+// less than a memset node between two kernels.
+cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st);
+
 // Specialised streaming decoder.  Decodes the longest prefix of whole chunks
 // it supports and returns the number of codewords covered in *covered (0 when
-// n has no specialised kernel).
+// n has no specialised kernel).  pdl: launched as the programmatic dependent
+// of a launch_zero_counts() just enqueued on `st`.
 cudaError_t launch_decode_fast(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
-                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered);
+                               int syn_type, unsigned long long *err, cudaStream_t st, uint64_t *covered,
+                               bool pdl = false);
 
 // The SECDED streaming decoder (codewords of n + 1 bits): whole chunks, as
 // launch_decode_fast; `det` (or nullptr) receives the detected double errors.
 cudaError_t launch_decode_fast_secded(const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
                                       int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
-                                      uint64_t *covered);
+                                      uint64_t *covered, bool pdl = false);
 
 // Decode table of n = 7 or 15 (data | s << k per codeword; with xh the SECDED
 // table of n + 1 bits, data | s << k | P << (k + m)), filled on `st` on first

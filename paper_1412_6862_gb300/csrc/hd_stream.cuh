@@ -36,7 +36,7 @@ struct StreamVariant {
     uint64_t chunk_cw;  // codewords per warp iteration (32*G)
     cudaError_t (*launch)(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out, void *syn,
                           unsigned long long *err, uint32_t *status, cudaStream_t st, unsigned long long *det,
-                          const uint16_t *lut);
+                          const uint16_t *lut, bool pdl);
     const void *kernel;
     int xh = 0;   // SECDED: codewords of n + 1 bits with the overall parity bit at position 0
     int lut = 0;  // decode table (n = 7, 15): one shared-memory lookup per codeword
@@ -354,6 +354,9 @@ __global__ void __launch_bounds__(T)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the counters were cleared by the kernel ahead of this one, which this
+        // launch may have overlapped (programmatic dependent launch)
+        grid_dep_wait();
         if (err != nullptr && s_counts[0] != 0) atomicAdd(err, s_counts[0]);
         if (XH && det != nullptr && s_counts[1] != 0) atomicAdd(det, s_counts[1]);
     }
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(T)
 template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
                                   void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
-                                  unsigned long long *det, const uint16_t *lut);
+                                  unsigned long long *det, const uint16_t *lut, bool pdl);
 
 // Per-device configuration of a kernel (dynamic shared memory opt-in and the
 // number of resident CTAs per SM).
@@ -371,7 +374,7 @@ int stream_blocks_per_sm(const void *kernel, int threads, uint32_t smem);
 template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH, bool LUT>
 cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, uint64_t nchunks, uint32_t *out,
                                   void *syn, unsigned long long *err, uint32_t *status, cudaStream_t st,
-                                  unsigned long long *det, const uint16_t *lut)
+                                  unsigned long long *det, const uint16_t *lut, bool pdl)
 {
     using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>;
     if (LUT && lut == nullptr) return cudaErrorInvalidValue;
@@ -381,6 +384,24 @@ cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, ui
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
     const int grid = decode_grid(want, cap);
+    if (pdl) {
+        // programmatic dependent launch: may start while the kernel ahead (the
+        // counters' clear) finishes; the kernel waits for it before counting
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(T);
+        cfg.dynamicSmemBytes = Cfg::smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr.val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e =
+            cudaLaunchKernelEx(&cfg, kern, in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
+        count_launch();
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
     count_launch();
     return cudaGetLastError();
