@@ -256,6 +256,9 @@ __global__ void __launch_bounds__(WARPS * 32)
 #pragma unroll
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
+        // the claim counter and the error counters are cleared by the kernel
+        // ahead of this one, which a programmatic dependent launch overlaps
+        grid_dep_wait();
         for (int s = 0; s < S; ++s) {
             const uint32_t t = atomicAdd(counter, 1u);
             DevTile d{};
@@ -419,16 +422,28 @@ struct BatchVariant {
     uint32_t smem;
     const void *kernel;
     void (*launch)(int grid, uint32_t smem, cudaStream_t st, const DevTile *, uint32_t, uint32_t *,
-                   unsigned long long *, uint32_t *, const uint16_t *, const uint16_t *);
+                   unsigned long long *, uint32_t *, const uint16_t *, const uint16_t *, bool pdl);
 };
 
 template <int W, int S, bool T15, int NSEL = 0>
 void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevTile *tiles, uint32_t num_tiles,
                          uint32_t *counter, unsigned long long *err, uint32_t *status, const uint16_t *lut7,
-                         const uint16_t *lut15)
+                         const uint16_t *lut15, bool pdl)
 {
-    k_decode_batch<W, S, T15, NSEL><<<grid, W * 32, smem, st>>>(tiles, num_tiles, counter, err, status, lut7,
-                                                                 lut15);
+    // the callers count batch launches (a plan's once per graph replay)
+    (void)launch_kernel_uncounted(k_decode_batch<W, S, T15, NSEL>, dim3((unsigned)grid), dim3(W * 32), smem, st, pdl,
+                                  tiles, num_tiles, counter, err, status, lut7, lut15);
+}
+
+// Clears a plan's claim counters and error counters, then lets the next
+// kernel of the stream start (programmatic dependent launch).
+__global__ void k_clear_plan(uint32_t *counters, uint32_t num_counters, unsigned long long *err, uint32_t num_err)
+{
+    grid_dep_launch_dependents();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (uint32_t j = i; j < num_counters; j += stride) counters[j] = 0u;
+    if (err != nullptr)
+        for (uint32_t j = i; j < num_err; j += stride) err[j] = 0ull;
 }
 
 template <int W, int S, bool T15 = false, int NSEL = 0>
@@ -638,13 +653,15 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
     uint32_t *status = g.status;
     cudaError_t e = cudaSuccess;
     if (clear) {
-        // one claim counter per code group (the split configuration), else the first
-        e = cudaMemsetAsync(p->d_counter, 0, sizeof(uint32_t) * (g.split ? kSplitGroups : 1), st);
-        if (e != cudaSuccess) return e;
-        if (err_counts) {
-            e = cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * p->num_packets, st);
-            if (e != cudaSuccess) return e;
-        }
+        // one claim counter per code group (the split configuration), else the
+        // first, and the error counters: one small kernel, which the single-kernel
+        // configurations' decode overlaps (programmatic dependent launch)
+        const uint32_t nc = g.split ? kSplitGroups : 1u;
+        const uint32_t work = std::max(nc, err_counts ? p->num_packets : 0u);
+        const int blocks = (int)std::min<uint32_t>(64u, (work + 255u) / 256u);
+        k_clear_plan<<<std::max(blocks, 1), 256, 0, st>>>(p->d_counter, nc, err_counts, p->num_packets);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (p->num_tiles == 0) return cudaSuccess;
     if (g.split) {
@@ -656,7 +673,7 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
             if ((e = cudaStreamWaitEvent(gs, p->fork, 0)) != cudaSuccess) return e;
             const BatchVariant &v = *g.gk[gi];
             v.launch(g.ggrid[gi], v.smem, gs, p->d_tiles + p->grp_begin[gi], p->grp_end[gi] - p->grp_begin[gi],
-                     p->d_counter + gi, err_counts, status, g.lut7, g.lut15);
+                     p->d_counter + gi, err_counts, status, g.lut7, g.lut15, false);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = cudaEventRecord(p->join[gi], gs)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(st, p->join[gi], 0)) != cudaSuccess) return e;
@@ -664,16 +681,16 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
         return cudaSuccess;
     }
     const BatchVariant &v = batch_variants()[g.variant];
-    v.launch(g.grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15);
+    v.launch(g.grid, v.smem, st, p->d_tiles, p->num_tiles, p->d_counter, err_counts, status, g.lut7, g.lut15, clear);
     return cudaGetLastError();
 }
 
 // Kernels enqueued by one launch of a prepared plan.
 uint64_t plan_kernels(const hd_plan *p, const LaunchGeom &g)
 {
-    if (p->num_tiles == 0) return 0;
-    if (!g.split) return 1;
-    uint64_t c = 0;
+    if (p->num_tiles == 0) return 1;  // the counters' clear
+    if (!g.split) return 2;
+    uint64_t c = 1;
     for (int gi = 0; gi < kSplitGroups; ++gi) c += g.gk[gi] != nullptr;
     return c;
 }
@@ -770,6 +787,7 @@ hd_status hd_plan_launch(hd_plan *p, unsigned long long *err_counts, void *cuda_
         if (prepare_plan(p, &geom, st) != cudaSuccess) return HD_ERR_CUDA;
         if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HD_ERR_CUDA;
         const cudaError_t e = enqueue_plan(p, geom, err_counts, p->capture);
+        g_launches.fetch_sub(1, std::memory_order_relaxed);  // the clear recorded here runs (and counts) per replay
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(p->capture, &g);
         if (e != cudaSuccess || e2 != cudaSuccess || g == nullptr) {
@@ -1038,7 +1056,7 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
     if (grid <= 0) return HD_ERR_CUDA;
     // no decode tables: this path never fills or synchronises anything
     v.launch(grid, v.smem, st, reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
-             g_noalloc_status[dev], nullptr, nullptr);
+             g_noalloc_status[dev], nullptr, nullptr, false);
     if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
     count_launch();
     return HD_OK;

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "hd.h"
@@ -47,6 +48,36 @@ cudaError_t launch_decode_generic(const uint32_t *in, uint64_t in_words, uint32_
                                   void *syn, int syn_type, unsigned long long *err, cudaStream_t st);
 cudaError_t launch_encode_generic(const uint32_t *data, uint64_t data_words, uint32_t n, uint64_t num_cw,
                                   uint32_t *stream, uint64_t stream_words, cudaStream_t st);
+
+// Launch `kern` on `st`, as the programmatic dependent of the kernel ahead of
+// it in the stream when pdl is set (it may then start before that kernel has
+// finished, and must wait for it before touching what that kernel writes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel_uncounted(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    bool pdl, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? &attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// launch_kernel_uncounted, counted in hd_launch_count().
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                          Args &&...args)
+{
+    count_launch();
+    return launch_kernel_uncounted(kern, grid, block, smem, st, pdl, std::forward<Args>(args)...);
+}
 
 // Clear one or two device counters (either may be NULL) with a one-thread
 // kernel that lets the next kernel of the stream start at once (programmatic

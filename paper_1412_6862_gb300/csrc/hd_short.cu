@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         dets += __shfl_xor_sync(0xFFFFFFFFu, dets, o);
     }
     if (lane == 0) {
+        grid_dep_wait();  // the counters' clear ahead of a programmatic dependent launch
         if (a.err && errs) atomicAdd(a.err, (unsigned long long)errs);
         if (a.det && dets) atomicAdd(a.det, (unsigned long long)dets);
     }
@@ -476,6 +477,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32)
         __syncwarp();
     }
     if (lane == 0) {
+        grid_dep_wait();  // the counters' clear ahead of a programmatic dependent launch
         if (err && errs) atomicAdd(err, (unsigned long long)errs);
         if (det && dets) atomicAdd(det, (unsigned long long)dets);
     }
@@ -535,13 +537,14 @@ struct ShortVariant {
     uint32_t stage_smem;  // dynamic shared memory of the warps' stages
     // [0]: table in global memory; [1]: table in shared memory; [2]: shared, splits in pass 3
     const void *kernel[3];
-    void (*launch[3])(const ShortArgs &, int grid, uint32_t smem, cudaStream_t);
+    cudaError_t (*launch[3])(const ShortArgs &, int grid, uint32_t smem, cudaStream_t, bool pdl);
 };
 
 template <int W, int S, int SB, bool TAB_SMEM, bool SPLIT>
-void launch_tiles(const ShortArgs &a, int grid, uint32_t smem, cudaStream_t st)
+cudaError_t launch_tiles(const ShortArgs &a, int grid, uint32_t smem, cudaStream_t st, bool pdl)
 {
-    k_short_tiles<W, S, SB, TAB_SMEM, SPLIT><<<grid, W * 32, smem, st>>>(a);
+    return launch_kernel(k_short_tiles<W, S, SB, TAB_SMEM, SPLIT>, dim3((unsigned)grid), dim3(W * 32), smem, st, pdl,
+                         a);
 }
 
 template <int W, int S, int SB>
@@ -804,7 +807,7 @@ void table_used(TableEntry *e, cudaStream_t st)
 
 cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t num_cw, uint32_t *out, void *syn,
                                int syn_type, unsigned long long *err, unsigned long long *det, cudaStream_t st,
-                               const void *table, uint32_t tab_len)
+                               const void *table, uint32_t tab_len, bool pdl = false)
 {
     const ShortVariant &v = kShortVariants[vi];
     const uint32_t r = short_r(n), k = n - r;
@@ -849,9 +852,7 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (a.ntiles + v.W - 1) / v.W;
     const int grid = decode_grid(want, cap);
-    v.launch[tsm](a, grid, smem, st);
-    count_launch();
-    return cudaGetLastError();
+    return v.launch[tsm](a, grid, smem, st, pdl);
 }
 
 }  // namespace
@@ -908,11 +909,12 @@ hd_status check_short_args(const uint32_t *stream, uint64_t in_bits, uint32_t n,
     return HD_OK;
 }
 
-// The decode itself, given the output-word table of n (unused for k < 64).
+// The decode itself, given the output-word table of n (unused for k < 64);
+// pdl: launched as the programmatic dependent of the counters' clear.
 hd_status decode_short_with(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64_t num_codewords,
                             uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
                             unsigned long long *err_count, unsigned long long *detected_count, cudaStream_t st,
-                            const void *table, uint32_t tab_len)
+                            const void *table, uint32_t tab_len, bool pdl)
 {
     const uint32_t r = short_r(n), k = n - r;
     const int syn = syndromes ? (int)syn_type : 0;
@@ -920,24 +922,28 @@ hd_status decode_short_with(const uint32_t *stream, uint64_t in_bits, uint32_t n
         int vi = current_short_variant(n);
         if (kShortVariants[vi].SB * 8u < n + 256u) vi = 1;  // stage too small for one codeword: largest stage
         if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
-                               st, table, tab_len) != cudaSuccess)
+                               st, table, tab_len, pdl) != cudaSuccess)
             return HD_ERR_CUDA;
         return HD_OK;
     }
     const uint64_t tiles = (num_codewords + 31) / 32;
     const uint64_t want = (tiles + kSmallWarps - 1) / kSmallWarps, cap = (uint64_t)num_sms() * 8;
-    k_short_small<<<decode_grid(want, cap), kSmallWarps * 32, 0, st>>>(
-        stream, words_for_bits(in_bits), n, r, num_codewords, out_bits, words_for_bits(num_codewords * k),
-        syndromes, syn, err_count, detected_count);
-    count_launch();
-    return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+    return launch_kernel(k_short_small, dim3((unsigned)decode_grid(want, cap)), dim3(kSmallWarps * 32), 0, st, pdl,
+                         stream, words_for_bits(in_bits), n, r, num_codewords, out_bits,
+                         words_for_bits(num_codewords * k), syndromes, syn, err_count, detected_count) == cudaSuccess
+               ? HD_OK
+               : HD_ERR_CUDA;
 }
 
-hd_status clear_counts(unsigned long long *err_count, unsigned long long *detected_count, cudaStream_t st)
+// Clear the counters (a one-thread kernel the decode may overlap); true when
+// the decode is to be launched as its programmatic dependent.
+hd_status clear_counts(unsigned long long *err_count, unsigned long long *detected_count, cudaStream_t st,
+                       bool *pdl)
 {
-    if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
-    if (detected_count && cudaMemsetAsync(detected_count, 0, sizeof(*detected_count), st) != cudaSuccess)
-        return HD_ERR_CUDA;
+    *pdl = false;
+    if (!err_count && !detected_count) return HD_OK;
+    if (launch_zero_counts(err_count, detected_count, st) != cudaSuccess) return HD_ERR_CUDA;
+    *pdl = true;
     return HD_OK;
 }
 
@@ -966,10 +972,11 @@ hd_status hd_decode_short(const uint32_t *stream, uint64_t in_bits, uint32_t n, 
         if (te == cudaErrorStreamCaptureUnsupported) return HD_ERR_INVALID_ARG;  // build it outside the capture
         if (te != cudaSuccess) return HD_ERR_CUDA;
     }
-    if ((rc = clear_counts(err_count, detected_count, st)) != HD_OK) return rc;
+    bool pdl = false;
+    if ((rc = clear_counts(err_count, detected_count, st, &pdl)) != HD_OK) return rc;
     if (num_codewords == 0) return HD_OK;
     rc = decode_short_with(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
-                           detected_count, st, e ? e->dev : nullptr, e ? e->len : 0);
+                           detected_count, st, e ? e->dev : nullptr, e ? e->len : 0, pdl);
     if (e && rc == HD_OK) table_used(e, st);
     return rc;
 }
@@ -1006,10 +1013,11 @@ hd_status hd_decode_short_plan(const hd_short_plan *plan, const uint32_t *stream
     if (cudaGetDevice(&dev) != cudaSuccess) return HD_ERR_CUDA;
     if (dev != plan->device) return HD_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if ((rc = clear_counts(err_count, detected_count, st)) != HD_OK) return rc;
+    bool pdl = false;
+    if ((rc = clear_counts(err_count, detected_count, st, &pdl)) != HD_OK) return rc;
     if (num_codewords == 0) return HD_OK;
     return decode_short_with(stream, in_bits, plan->n, num_codewords, out_bits, syndromes, syn_type, err_count,
-                             detected_count, st, plan->table, plan->tab_len);
+                             detected_count, st, plan->table, plan->tab_len, pdl);
 }
 
 void hd_short_plan_destroy(hd_short_plan *plan)

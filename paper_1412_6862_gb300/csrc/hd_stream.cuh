@@ -384,27 +384,10 @@ cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, ui
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
     const int grid = decode_grid(want, cap);
-    if (pdl) {
-        // programmatic dependent launch: may start while the kernel ahead (the
-        // counters' clear) finishes; the kernel waits for it before counting
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3(T);
-        cfg.dynamicSmemBytes = Cfg::smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr.val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        const cudaError_t e =
-            cudaLaunchKernelEx(&cfg, kern, in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
-        count_launch();
-        return e != cudaSuccess ? e : cudaGetLastError();
-    }
-    kern<<<grid, T, Cfg::smem, st>>>(in, out, static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
-    count_launch();
-    return cudaGetLastError();
+    // with pdl the launch may overlap the counters' clear ahead of it; the
+    // kernel waits for that clear before it counts
+    return launch_kernel(kern, dim3((unsigned)grid), dim3(T), Cfg::smem, st, pdl, in, out,
+                         static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
 }
 
 template <int N_, int SYN, int T, int S, int G, int INPLACE, bool XH = false, bool LUT = false>
