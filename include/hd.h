@@ -80,6 +80,30 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
                     uint32_t *out_bits, void *syndromes, hd_syn_type syn_type,
                     unsigned long long *err_count, void *cuda_stream);
 
+/* Several independent streams decoded concurrently.  Each job is one
+ * hd_decode() call (arguments, layout, results and errors as there, with
+ * in_bits = n * num_codewords).  The jobs' counters are cleared by one kernel
+ * on `cuda_stream`, then the decodes run as concurrent branches forked from
+ * `cuda_stream` onto library-owned streams (8 per device, created by the
+ * first call on a device, which should come before any stream capture) and
+ * joined back into it, largest stream first: work enqueued on `cuda_stream`
+ * after this call waits for every job.  Decoding the streams side by side lets
+ * one decode's ramp-up and drain overlap another's steady state, the
+ * pipelining of independent packets the paper applies to its transfers
+ * (Sec. III-B).  At most 32 jobs per call (HD_ERR_CAPACITY); the jobs' output
+ * buffers must not overlap.  Calls from several host threads are serialised. */
+typedef struct {
+    const uint32_t *stream;
+    uint32_t *out_bits;
+    void *syndromes;
+    unsigned long long *err_count;
+    uint64_t num_codewords;
+    uint32_t n;
+    uint32_t syn_type; /* an hd_syn_type */
+} hd_stream_job;
+
+hd_status hd_decode_streams(const hd_stream_job *jobs, uint32_t num_jobs, void *cuda_stream);
+
 /* Decode from and to HOST memory with overlapped transfers -- the paper's
  * asynchronous data transfer (Sec. III-B, Fig. 5, Eq. 1).  The stream is cut
  * into chunks of `chunk_codewords` (a multiple of 128; 0 = 2^22) and each

@@ -155,7 +155,7 @@ struct StreamCfg : ChunkGeom<N_, SYN, G, XH> {
     static constexpr uint32_t lut_bytes = LUT ? (2u << (N_ + (XH ? 1 : 0))) : 0u;  // u16 per codeword value
     static constexpr uint32_t off_lut = WARPS * warp_bytes;         // the table, then its mbarrier
     static constexpr uint32_t smem = off_lut + (LUT ? lut_bytes + 16u : 0u);
-    static constexpr bool fits = smem + 64 <= 232448;  // the opt-in maximum per CTA (with the static counts)
+    static constexpr bool fits = smem <= 232448;  // the opt-in maximum per CTA
     static_assert(T % 32 == 0 && S <= 8, "whole warps, at most 8 stages");
     static_assert(!INPLACE || Q::out_bytes + 16 <= stage_bytes, "in-place output fits the input stage");
     static_assert(!INPLACE || S >= 2, "in-place refills lag one iteration");
@@ -335,30 +335,16 @@ __global__ void __launch_bounds__(T)
         }
         bulk_wait_all<0>();
     }
-    // counts: warp sums, then one shared-memory sum per CTA, then one global
-    // atomic per CTA (thousands of warps adding to one address serialise at
-    // the end of the launch)
-    __shared__ unsigned long long s_counts[2];
-    if (threadIdx.x == 0) {
-        s_counts[0] = 0;
-        s_counts[1] = 0;
-    }
-    __syncthreads();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
-    if (lane == 0 && errs != 0) atomicAdd(&s_counts[0], (unsigned long long)errs);
     if constexpr (XH) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dets += __shfl_xor_sync(0xFFFFFFFFu, dets, o);
-        if (lane == 0 && dets != 0) atomicAdd(&s_counts[1], (unsigned long long)dets);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // the counters were cleared by the kernel ahead of this one, which this
-        // launch may have overlapped (programmatic dependent launch)
+    if (lane == 0) {
         grid_dep_wait();
-        if (err != nullptr && s_counts[0] != 0) atomicAdd(err, s_counts[0]);
-        if (XH && det != nullptr && s_counts[1] != 0) atomicAdd(det, s_counts[1]);
+        if (err != nullptr && errs != 0) atomicAdd(err, (unsigned long long)errs);
+        if (XH && det != nullptr && dets != 0) atomicAdd(det, (unsigned long long)dets);
     }
 }
 

@@ -64,6 +64,12 @@ class PlanInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class StreamJob(ctypes.Structure):
+    """Mirror of hd_stream_job."""
+    _fields_ = [("stream", _vp), ("out_bits", _vp), ("syndromes", _vp), ("err_count", _vp),
+                ("num_codewords", _u64), ("n", _u32), ("syn_type", _u32)]
+
+
 class HostJob(ctypes.Structure):
     _fields_ = [("host_stream", _c.c_void_p), ("host_out", _c.c_void_p), ("host_syndromes", _c.c_void_p),
                 ("host_err_count", _c.c_void_p), ("num_codewords", _c.c_uint64), ("n", _c.c_uint32),
@@ -109,6 +115,7 @@ SIGNATURES = {
     "hd_variant_current": (_i32, [_u32, _i32, _VIP]),
     "hd_autotune": (_i32, [_u32, _i32, _u64, _u32, _vp, _VIP]),
     "hd_decode": (_i32, [_vp, _u64, _u32, _u64, _vp, _vp, _i32, _vp, _vp]),
+    "hd_decode_streams": (_i32, [_c.POINTER(StreamJob), _u32, _vp]),
     "hd_plan_create": (_i32, [_PKP, _u32, _c.POINTER(_vp)]),
     "hd_plan_launch": (_i32, [_vp, _vp, _vp]),
     "hd_plan_autotune": (_i32, [_vp, _u32, _vp, _PIP]),
@@ -202,6 +209,18 @@ def check(status: int, what: str = "") -> None:
 def hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, cuda_stream) -> int:
     return lib().hd_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count,
                            cuda_stream)
+
+
+def stream_jobs(jobs) -> ctypes.Array:
+    """ctypes array of hd_stream_job from (stream_ptr, n, num_codewords, out_ptr, syn_ptr, syn_type, err_ptr)."""
+    arr = (StreamJob * max(1, len(jobs)))()
+    for i, (a, n, N, o, sy, st, e) in enumerate(jobs):
+        arr[i] = StreamJob(a, o, sy, e, N, n, st if sy else SYN_NONE)
+    return arr
+
+
+def hd_decode_streams(jobs_array, num_jobs: int, cuda_stream) -> int:
+    return lib().hd_decode_streams(jobs_array, num_jobs, cuda_stream)
 
 
 def hd_decode_host(host_stream, in_bits, n, num_codewords, host_out, host_syndromes, syn_type, chunk_codewords=0,

@@ -132,3 +132,55 @@ FULL = [(7, 1 << 20, hd.SYN_U8), (15, 1 << 24, hd.SYN_U8), (31, 1 << 24, hd.SYN_
 def test_parity_full_size(n, N, syn):
     p1, p2 = {7: (0.1, 0.0), 127: (0.05, 0.005), 255: (0.05, 0.005)}.get(n, (0.1, 0.01))
     run_case(n, N, syn, seed=0, p1=p1, p2=p2)
+
+
+def _streams_case(seed):
+    import torch
+    specs = [(63, 3 * 8192 + 5, hd.SYN_U8), (15, 70001, hd.SYN_U8), (255, 9001, hd.SYN_U16), (7, 1, hd.SYN_NONE),
+             (31, 50000, hd.SYN_U16), (127, 4099, hd.SYN_U8), (3, 777, hd.SYN_U8), (31, 0, hd.SYN_U8)]
+    jobs, bufs, exp = [], [], []
+    for i, (n, N, st) in enumerate(specs):
+        m, k = hd.code_params(n)
+        stream, _, _ = gc.received_stream(n, N, seed=seed + i, p1=0.2, p2=0.02)
+        exp.append(gc.expected(stream, n, N, st) if N else (np.zeros(0, np.uint32), None, 0))
+        d_in = gc.to_device(stream)
+        out = torch.full((max(1, hd.words_for(N * k)),), -1, dtype=torch.int32, device="cuda")
+        syn = None if st == hd.SYN_NONE else torch.full((max(1, N),), 0x55, dtype=torch.uint8 if st == 1 else
+                                                         torch.int16, device="cuda")
+        err = torch.full((1,), 999, dtype=torch.int64, device="cuda")
+        bufs.append((d_in, out, syn, err, n, N, st))
+        jobs.append((d_in.data_ptr(), n, N, out.data_ptr(), None if syn is None else syn.data_ptr(), st,
+                     err.data_ptr()))
+    return hd.stream_jobs(jobs), bufs, exp
+
+
+def _streams_check(bufs, exp):
+    for (d_in, out, syn, err, n, N, st), (eo, es, ee) in zip(bufs, exp):
+        if N == 0:
+            assert int(err.item()) == 0
+            continue
+        gc.assert_same((out, syn, err), (eo, es, ee), n, N, st)
+
+
+def test_decode_streams_matches_oracle_directly_and_in_a_graph():
+    """Several streams of different n decoded concurrently (hd_decode_streams):
+    every element equals the oracle's, called directly and replayed from a
+    captured CUDA graph."""
+    import torch
+    jobs, bufs, exp = _streams_case(seed=500)
+    rc = hd.hd_decode_streams(jobs, len(bufs), torch.cuda.current_stream().cuda_stream)
+    assert rc == hd.HD_OK
+    torch.cuda.synchronize()
+    _streams_check(bufs, exp)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert hd.hd_decode_streams(jobs, len(bufs), s.cuda_stream) == hd.HD_OK
+    for _ in range(2):
+        for (d_in, out, syn, err, n, N, st) in bufs:
+            out.fill_(-1)
+            err.fill_(12345)
+        g.replay()
+        torch.cuda.synchronize()
+        _streams_check(bufs, exp)
+    assert hd.hd_device_status() == 0

@@ -222,3 +222,18 @@ def test_secded_variants_host_only(lib):
             assert hd.hd_secded_variant_count(n, syn) == (2 if n in (7, 15) else 1)
     assert hd.lib().hd_secded_variant_count(9, 0, None) in (hd.HD_ERR_NULL, hd.HD_ERR_INVALID_N)
     assert hd.lib().hd_secded_variant_select(9, 0, 0) == hd.HD_ERR_INVALID_N
+
+
+def test_decode_streams_validation_host_only(lib):
+    # rejected on the host before any device work; the pointers are never used
+    assert hd.hd_decode_streams(None, 2, None) == hd.HD_ERR_NULL
+    assert hd.hd_decode_streams(None, 0, None) == hd.HD_OK
+    many = hd.stream_jobs([(16, 7, 32, 16, None, 0, None)] * 33)
+    assert hd.hd_decode_streams(many, 33, None) == hd.HD_ERR_CAPACITY
+    bad_n = hd.stream_jobs([(16, 7, 32, 16, None, 0, None), (16, 9, 32, 16, None, 0, None)])
+    assert hd.hd_decode_streams(bad_n, 2, None) == hd.HD_ERR_INVALID_N
+    unaligned = hd.stream_jobs([(20, 7, 32, 16, None, 0, None)])
+    assert hd.hd_decode_streams(unaligned, 1, None) == hd.HD_ERR_ALIGN
+    no_syn = hd.stream_jobs([(16, 7, 32, 16, None, 0, None)])
+    no_syn[0].syn_type = hd.SYN_U8  # a syndrome type without a buffer
+    assert hd.hd_decode_streams(no_syn, 1, None) == hd.HD_ERR_NULL
