@@ -5,16 +5,16 @@
 // cut into full warp chunks of 32*G codewords (G = 32 for n <= 31, 16 for
 // n = 63, 8 for n = 127; n = 255 takes half-warp chunks of 16*8, so a chunk's
 // input is at most 4 KB) and, when its length is not a multiple of that, one
-// ragged tail tile.  Warps of a
-// persistent kernel claim tiles from an atomic counter in table order (tiles
-// grouped by n, each code's tails spread among its full tiles), prefetch
-// claimed tiles into their own shared-memory stages with 1-D bulk copies,
-// decode full tiles with the same per-warp chunk decoder as the streaming
-// kernel, decode tails with the chunk decoder too (copied in, zero-padded to a
+// ragged tail tile.  The tiles of a
+// persistent kernel are dealt round-robin to its warps in table order (tiles
+// grouped by n, each code's tails spread among its full tiles); a warp
+// prefetches its tiles into its own shared-memory stages with 1-D bulk copies,
+// decodes full tiles with the same per-warp chunk decoder as the streaming
+// kernel, decodes tails with the chunk decoder too (copied in, zero-padded to a
 // chunk, copied back out; n = 3 tails use the generic warp-tile decoder), and
-// add each tile's nonzero-syndrome count to its packet's error counter.
-// Dynamic claiming of bounded tiles balances packets whose lengths span six
-// orders of magnitude.
+// adds each tile's nonzero-syndrome count to its packet's error counter.
+// Cutting packets whose lengths span six orders of magnitude into bounded
+// tiles is what balances the load.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -247,9 +247,19 @@ __global__ void __launch_bounds__(WARPS * 32)
             mbar_arrive(&bar[s]);
         }
     };
-    // Claims run one iteration ahead of their use: the atomic issued while a
-    // tile is decoded returns long before its result is needed, and the
-    // claimed tile's descriptor is fetched during the next decode.
+    // Tiles are dealt round-robin: warp gw takes tiles gw, gw + tw, gw + 2 tw,
+    // ... (tw warps in the grid).  Tiles are bounded (at most 4 KB of input),
+    // so this balances as well as claiming from a shared counter, without the
+    // atomic on one address that every warp would otherwise issue per tile
+    // (tens of thousands per launch, serialised at that address).  The next
+    // tile's descriptor is fetched one iteration ahead, during a decode.
+    const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (uint64_t)warp, tw = (uint64_t)gridDim.x * WARPS;
+    uint32_t seq = 0;  // lane 0: tiles dealt to this warp so far
+    auto deal = [&]() -> uint32_t {
+        const uint64_t t = gw + (uint64_t)(seq++) * tw;
+        return t < (uint64_t)num_tiles ? (uint32_t)t : num_tiles;
+    };
+    (void)counter;  // the claim counter of dynamic claiming; dealing needs none
     uint32_t next_t = 0;
     DevTile next_d{};
     if (lane == 0) {
@@ -260,12 +270,12 @@ __global__ void __launch_bounds__(WARPS * 32)
         // ahead of this one, which a programmatic dependent launch overlaps
         grid_dep_wait();
         for (int s = 0; s < S; ++s) {
-            const uint32_t t = atomicAdd(counter, 1u);
+            const uint32_t t = deal();
             DevTile d{};
             if (t < num_tiles) d = tiles[t];
             issue(s, t, d);
         }
-        next_t = atomicAdd(counter, 1u);
+        next_t = deal();
     }
     __syncwarp();
 
@@ -287,7 +297,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         uint32_t later_t = 0;
         if (lane == 0 && it > 0) {
             if (next_t < num_tiles) next_d = tiles[next_t];  // used at the end of this iteration
-            later_t = atomicAdd(counter, 1u);                // used at the end of the next one
+            later_t = deal();                                 // used at the end of the next one
         }
         const DevTile tl = desc[s];  // written by lane 0 before the stage's arrive
         struct {
