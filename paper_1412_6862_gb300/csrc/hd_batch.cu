@@ -5,10 +5,10 @@
 // cut into full warp chunks of 32*G codewords (G = 32 for n <= 31, 16 for
 // n = 63, 8 for n = 127; n = 255 takes half-warp chunks of 16*8, so a chunk's
 // input is at most 4 KB) and, when its length is not a multiple of that, one
-// ragged tail tile.  The tiles of a
-// persistent kernel are dealt round-robin to its warps in table order (tiles
-// grouped by n, each code's tails spread among its full tiles); a warp
-// prefetches its tiles into its own shared-memory stages with 1-D bulk copies,
+// ragged tail tile.  The warps of a
+// persistent kernel take tiles in table order (tiles grouped by n, each
+// code's tails spread among its full tiles; claimed from an atomic counter, or
+// dealt round-robin by the single-n kernels), prefetch their tiles into its own shared-memory stages with 1-D bulk copies,
 // decodes full tiles with the same per-warp chunk decoder as the streaming
 // kernel, decodes tails with the chunk decoder too (copied in, zero-padded to a
 // chunk, copied back out; n = 3 tails use the generic warp-tile decoder), and
@@ -247,19 +247,24 @@ __global__ void __launch_bounds__(WARPS * 32)
             mbar_arrive(&bar[s]);
         }
     };
-    // Tiles are dealt round-robin: warp gw takes tiles gw, gw + tw, gw + 2 tw,
-    // ... (tw warps in the grid).  Tiles are bounded (at most 4 KB of input),
-    // so this balances as well as claiming from a shared counter, without the
-    // atomic on one address that every warp would otherwise issue per tile
-    // (tens of thousands per launch, serialised at that address).  The next
-    // tile's descriptor is fetched one iteration ahead, during a decode.
+    // Which tile a warp takes next.  The single-n kernels (NSEL != 0) deal
+    // tiles round-robin: warp gw takes tiles gw, gw + tw, gw + 2 tw, ... (tw
+    // warps in the grid), which balances their tiles of one code without an
+    // atomic per tile on one shared address.  The all-n kernel, whose tiles
+    // differ more in cost, claims them from the atomic counter, so that a warp
+    // that finished early takes more (measured: 250 µs claimed against 267 µs
+    // dealt for it; 246 against 239 µs for the single-n kernels).  Either way the
+    // next tile is claimed, and its descriptor fetched, one iteration ahead.
     const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (uint64_t)warp, tw = (uint64_t)gridDim.x * WARPS;
     uint32_t seq = 0;  // lane 0: tiles dealt to this warp so far
     auto deal = [&]() -> uint32_t {
-        const uint64_t t = gw + (uint64_t)(seq++) * tw;
-        return t < (uint64_t)num_tiles ? (uint32_t)t : num_tiles;
+        if constexpr (NSEL == 0) {
+            return atomicAdd(counter, 1u);
+        } else {
+            const uint64_t t = gw + (uint64_t)(seq++) * tw;
+            return t < (uint64_t)num_tiles ? (uint32_t)t : num_tiles;
+        }
     };
-    (void)counter;  // the claim counter of dynamic claiming; dealing needs none
     uint32_t next_t = 0;
     DevTile next_d{};
     if (lane == 0) {

@@ -17,6 +17,18 @@ void register_stream_secded(std::vector<StreamVariant> &v)
     // decode tables (one lookup per codeword; used when the table is filled)
     add_variants<7, 128, 4, 32, 1, true, true>(v);
     add_variants<15, 512, 2, 32, 1, true, true>(v);  // 128 KB table per CTA
+    // further configurations, selectable with hd_secded_variant_select
+    add_variants<31, 128, 2, 32, 1, true>(v);
+    add_variants<31, 256, 2, 32, 1, true>(v);
+    add_variants<63, 64, 2, 32, 1, true>(v);
+    add_variants<63, 128, 3, 32, 1, true>(v);
+    add_variants<127, 256, 3, 8, 1, true>(v);
+    add_variants<127, 128, 3, 8, 1, true>(v);
+    add_variants<127, 64, 3, 16, 1, true>(v);
+    add_variants<127, 128, 2, 16, 1, true>(v);
+    add_variants<255, 128, 3, 8, 1, true>(v);
+    add_variants<255, 64, 2, 16, 1, true>(v);
+    add_variants<15, 384, 2, 32, 1, true, true>(v);
 }
 
 }  // namespace hd
