@@ -265,8 +265,13 @@ __global__ void __launch_bounds__(WARPS * 32)
             return t < (uint64_t)num_tiles ? (uint32_t)t : num_tiles;
         }
     };
-    uint32_t next_t = 0;
-    DevTile next_d{};
+    // The single-n kernels fetch a descriptor two iterations before its tile
+    // is issued (next_d is in registers when its refill is due, after_d is in
+    // flight), since one of their decodes can be shorter than a load from L2;
+    // the all-n kernel, at its register limit, fetches one iteration ahead.
+    constexpr bool kAhead2 = NSEL != 0;
+    uint32_t next_t = 0, after_t = 0;
+    DevTile next_d{}, after_d{};
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
@@ -281,6 +286,10 @@ __global__ void __launch_bounds__(WARPS * 32)
             issue(s, t, d);
         }
         next_t = deal();
+        if constexpr (kAhead2) {
+            if (next_t < num_tiles) next_d = tiles[next_t];  // issued at the end of iteration 1
+            after_t = deal();
+        }
     }
     __syncwarp();
 
@@ -301,8 +310,12 @@ __global__ void __launch_bounds__(WARPS * 32)
         // last iteration and claim the next one
         uint32_t later_t = 0;
         if (lane == 0 && it > 0) {
-            if (next_t < num_tiles) next_d = tiles[next_t];  // used at the end of this iteration
-            later_t = deal();                                 // used at the end of the next one
+            if constexpr (kAhead2) {
+                if (after_t < num_tiles) after_d = tiles[after_t];  // used at the end of the next iteration
+            } else {
+                if (next_t < num_tiles) next_d = tiles[next_t];  // used at the end of this iteration
+            }
+            later_t = deal();  // its descriptor is fetched next iteration
         }
         const DevTile tl = desc[s];  // written by lane 0 before the stage's arrive
         struct {
@@ -403,7 +416,13 @@ __global__ void __launch_bounds__(WARPS * 32)
             if (it > 0) {
                 bulk_wait_read<0>();
                 issue((int)((it - 1) % S), next_t, next_d);
-                next_t = later_t;
+                if constexpr (kAhead2) {
+                    next_t = after_t;
+                    next_d = after_d;
+                    after_t = later_t;
+                } else {
+                    next_t = later_t;
+                }
             }
             if (full) {
                 const uint32_t cw = tl.count & ~kFullTile;
