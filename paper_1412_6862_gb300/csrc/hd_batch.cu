@@ -505,21 +505,19 @@ struct SplitKernels {
     BatchVariant n15_table;
 };
 
-const SplitKernels &split_kernels()
+template <int W, int S>
+SplitKernels make_split_kernels()
 {
-    static const SplitKernels k = [] {
-        SplitKernels s;
-        s.group[0] = make_batch_variant<1, 3, false, 255>();
-        s.group[1] = make_batch_variant<1, 3, false, 127>();
-        s.group[2] = make_batch_variant<1, 3, false, 63>();
-        s.group[3] = make_batch_variant<1, 3, false, 31>();
-        s.group[4] = make_batch_variant<1, 3, false, 15>();
-        s.group[5] = make_batch_variant<1, 3, false, 7>();
-        s.group[6] = make_batch_variant<1, 3, false, 3>();
-        s.n15_table = make_batch_variant<12, 2, true, 15>();
-        return s;
-    }();
-    return k;
+    SplitKernels s;
+    s.group[0] = make_batch_variant<W, S, false, 255>();
+    s.group[1] = make_batch_variant<W, S, false, 127>();
+    s.group[2] = make_batch_variant<W, S, false, 63>();
+    s.group[3] = make_batch_variant<W, S, false, 31>();
+    s.group[4] = make_batch_variant<W, S, false, 15>();
+    s.group[5] = make_batch_variant<W, S, false, 7>();
+    s.group[6] = make_batch_variant<W, S, false, 3>();
+    s.n15_table = make_batch_variant<12, 2, true, 15>();
+    return s;
 }
 
 static const std::vector<BatchVariant> &batch_variants()
@@ -533,6 +531,15 @@ static const std::vector<BatchVariant> &batch_variants()
     return v;
 }
 
+// The split configurations: warps per CTA and stages of the single-n kernels
+// (their 64-96 registers leave room for multi-warp CTAs, which the all-n
+// kernel's 128 or more do not).
+const std::vector<SplitKernels> &split_kernels()
+{
+    static const std::vector<SplitKernels> k = {make_split_kernels<1, 3>(), make_split_kernels<4, 2>(),
+                                                make_split_kernels<2, 3>()};
+    return k;
+}
 }  // namespace hd
 
 using namespace hd;
@@ -650,9 +657,10 @@ struct LaunchGeom {
     int ggrid[kSplitGroups] = {};
 };
 
-// Index of the split configuration among a plan's configurations (after the
-// single-kernel ones).
+// Index of the first split configuration among a plan's configurations
+// (after the single-kernel ones), and the number of configurations.
 inline int split_variant() { return (int)batch_variants().size(); }
+inline int plan_variants() { return split_variant() + (int)split_kernels().size(); }
 
 cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
 {
@@ -660,11 +668,11 @@ cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
     if (g->status == nullptr) return cudaErrorInvalidSymbol;
     g->variant = p->variant;
     g->lut7 = lut_ptr(7, st);
-    if (g->variant == split_variant()) {
+    if (g->variant >= split_variant()) {
         g->split = true;
         g->lut15 = lut_ptr(15, st);
         g->grid = 0;
-        const SplitKernels &sk = split_kernels();
+        const SplitKernels &sk = split_kernels()[g->variant - split_variant()];
         for (int gi = 0; gi < kSplitGroups; ++gi) {
             const uint32_t nt = p->grp_end[gi] - p->grp_begin[gi];
             if (nt == 0) continue;
@@ -853,7 +861,7 @@ hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan
     float best_us = 0.f;
     const int keep = p->variant;
     hd_status rc = HD_OK;
-    for (int i = 0; i <= split_variant(); ++i) {
+    for (int i = 0; i < plan_variants(); ++i) {
         p->variant = i;
         LaunchGeom geom;
         if (prepare_plan(p, &geom, st) != cudaSuccess || geom.variant != (int)i) continue;
@@ -890,8 +898,9 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
 {
     if (!p || !info) return HD_ERR_NULL;
     std::memset(info, 0, sizeof(*info));
-    const bool split = p->variant == split_variant();
-    const BatchVariant &v = split ? split_kernels().group[0] : batch_variants()[p->variant];
+    const bool split = p->variant >= split_variant();
+    const BatchVariant &v = split ? split_kernels()[p->variant - split_variant()].group[0]
+                                  : batch_variants()[p->variant];
     info->num_packets = p->num_packets;
     info->num_tiles = p->num_tiles;
     info->full_tiles = p->full_tiles;
@@ -903,7 +912,7 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
     info->stages = (uint32_t)v.stages;
     info->smem_bytes = v.smem;
     info->variant = (uint32_t)p->variant;
-    info->num_variants = (uint32_t)split_variant() + 1;
+    info->num_variants = (uint32_t)plan_variants();
     info->measured_us = p->tuned_us;
     info->table_lookup = 1u | (v.t15 || split ? 2u : 0u);
     return HD_OK;
@@ -912,7 +921,7 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
 hd_status hd_plan_select(hd_plan *p, uint32_t variant)
 {
     if (!p) return HD_ERR_NULL;
-    if (variant > (uint32_t)split_variant()) return HD_ERR_INVALID_ARG;
+    if (variant >= (uint32_t)plan_variants()) return HD_ERR_INVALID_ARG;
     p->variant = (int)variant;
     drop_graph(p);
     return HD_OK;
