@@ -430,9 +430,10 @@ hd_status hd_decode_batch(const hd_packet *table, uint32_t num_packets, unsigned
  * the claim counter is cleared on `cuda_stream` at the start of each call,
  * and two calls that overlap on the GPU (for example on two streams) race on
  * the array, so order them on one stream or synchronise between them.  The
- * tables are copied from pageable host memory, so the call waits for earlier
- * work on `cuda_stream` before it returns.  Calls from several host threads
- * are serialised.  err_counts is overwritten as in hd_decode_batch(). */
+ * tile table reaches the array through small upload kernels that carry up to
+ * 480 tiles each in their launch parameters, so the call needs no host-side
+ * staging and returns without waiting for the GPU.  Calls from several host
+ * threads are serialised.  err_counts is overwritten as in hd_decode_batch(). */
 hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t num_packets, unsigned long long *err_counts,
                                   void *cuda_stream);
 

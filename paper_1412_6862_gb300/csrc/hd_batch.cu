@@ -998,11 +998,23 @@ static_assert(sizeof(DevTile) == 64, "table layout");
 // cudaGetSymbolAddress; kernels receive the device address it returns.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Host image of the tile table, uploaded with one copy.  The copy reads
-// pageable memory, so it has consumed it when cudaMemcpyAsync returns and the
-// next call may rewrite it; the mutex serialises host threads.
-alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
-std::mutex g_noalloc_mu;
+// The tile table reaches the array through kernel parameters: each upload
+// launch carries up to kUploadTiles descriptors by value (within the 32 KB
+// parameter limit), so no host staging and no host-to-device copy is needed.
+constexpr uint32_t kUploadTiles = 480;
+struct TileUpload {
+    DevTile tiles[kUploadTiles];
+    uint32_t first;  // index of tiles[0] in the table
+    uint32_t count;
+};
+static_assert(sizeof(TileUpload) <= 32000, "kernel parameter space");
+
+__global__ void k_upload_tiles(const __grid_constant__ TileUpload u, DevTile *__restrict__ table)
+{
+    for (uint32_t i = threadIdx.x; i < u.count; i += blockDim.x) table[u.first + i] = u.tiles[i];
+}
+
+std::mutex g_noalloc_mu;  // serialises host threads (the device array is shared)
 constexpr int kNoAllocMaxDevices = 64;
 unsigned char *g_noalloc_dev[kNoAllocMaxDevices];  // device address of the scratch, per device
 uint32_t *g_noalloc_status[kNoAllocMaxDevices];
@@ -1071,9 +1083,28 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
     unsigned char *dbase = g_noalloc_dev[dev];
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // host image: tiles grouped by n (long codes first), each code's tails among its full tiles
-    DevTile *ht = reinterpret_cast<DevTile *>(g_noalloc_host + kNoAllocTilesOff);
+    // the claim counter must start at zero; the error counters are overwritten
+    uint32_t *counter = reinterpret_cast<uint32_t *>(dbase);
+    DevTile *dtab = reinterpret_cast<DevTile *>(dbase + kNoAllocTilesOff);
+    if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess) return HD_ERR_CUDA;
+    if (err_counts && num_packets &&
+        cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * num_packets, st) != cudaSuccess)
+        return HD_ERR_CUDA;
+    // tiles grouped by n (long codes first), each code's tails among its full
+    // tiles, uploaded kUploadTiles at a time by kernels that carry them
+    static TileUpload up;  // 30 KB, off the thread's stack; guarded by g_noalloc_mu
+    up.first = 0;
+    up.count = 0;
     uint32_t t = 0;
+    bool ok = true;
+    auto flush = [&]() {
+        if (up.count == 0 || !ok) return;
+        k_upload_tiles<<<1, 128, 0, st>>>(up, dtab);
+        count_launch();
+        ok = cudaGetLastError() == cudaSuccess;
+        up.first += up.count;
+        up.count = 0;
+    };
     static const uint32_t order[] = {255, 127, 63, 31, 15, 7, 3};
     for (uint32_t n : order)
         emit_code_tiles(
@@ -1083,23 +1114,19 @@ extern "C" hd_status hd_decode_batch_noalloc(const hd_packet *table, uint32_t nu
                 return PacketView{q.in, q.out, static_cast<uint8_t *>(q.syndromes), q.num_codewords, q.n,
                                   (uint32_t)code_m(q.n), q.syndromes ? q.syn_type : 0u};
             },
-            [&](const DevTile &tile) { ht[t++] = tile; });
-
-    // the claim counter must start at zero; the error counters are overwritten
-    uint32_t *counter = reinterpret_cast<uint32_t *>(dbase);
-    if (cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess) return HD_ERR_CUDA;
-    if (err_counts && num_packets &&
-        cudaMemsetAsync(err_counts, 0, sizeof(unsigned long long) * num_packets, st) != cudaSuccess)
-        return HD_ERR_CUDA;
+            [&](const DevTile &tile) {
+                up.tiles[up.count++] = tile;
+                ++t;
+                if (up.count == kUploadTiles) flush();
+            });
+    flush();
+    if (!ok) return HD_ERR_CUDA;
     if (t == 0) return HD_OK;
-    if (cudaMemcpyAsync(dbase + kNoAllocTilesOff, ht, sizeof(DevTile) * t, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return HD_ERR_CUDA;
     const BatchVariant &v = batch_variants()[0];
     const int grid = batch_grid(v, t);
     if (grid <= 0) return HD_ERR_CUDA;
     // no decode tables: this path never fills or synchronises anything
-    v.launch(grid, v.smem, st, reinterpret_cast<const DevTile *>(dbase + kNoAllocTilesOff), t, counter, err_counts,
-             g_noalloc_status[dev], nullptr, nullptr, false);
+    v.launch(grid, v.smem, st, dtab, t, counter, err_counts, g_noalloc_status[dev], nullptr, nullptr, false);
     if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
     count_launch();
     return HD_OK;

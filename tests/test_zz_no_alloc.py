@@ -86,6 +86,7 @@ def test_noalloc_matches_allocating_batch_two_calls():
     assert expect_err.sum() > 0
 
     table = _table(mine)
+    assert hd.hd_batch_tiles(table, num) > 2 * 480  # several upload launches of the tile table
     err = torch.empty(num, dtype=torch.int64, device="cuda")
     for call in range(2):
         for (_, out, syn, _, _, _) in mine:  # stale results must not mask a failure
