@@ -62,6 +62,22 @@ __host__ __device__ constexpr uint64_t batch_chunk_cw(uint32_t n)
 // and load latency are amortised.
 __host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 7 ? 4 : (n <= 15 ? 2 : 1); }
 
+// The long codes' geometry in the split configuration (BIG): the streaming
+// kernel's chunk shapes in 8 KB stages -- n = 63 with 32 codewords per thread
+// (1024 per chunk, 8064 bytes), n = 127 with two 256-codeword chunks per tile
+// (8128 bytes), n = 255 with full-warp chunks of 256 codewords (8160 bytes) --
+// so that a tile holds twice the work of the 4 KB tiles, and n = 63 and 255
+// decode whole 32-codeword tiles per thread part.  Other codes keep the
+// 4 KB geometry.
+__host__ __device__ constexpr bool big_geometry(uint32_t n) { return n == 63 || n == 127 || n == 255; }
+__host__ __device__ constexpr int geo_G(uint32_t n, bool big) { return big && n == 63 ? 32 : batch_G(n); }
+__host__ __device__ constexpr int geo_lanes(uint32_t n, bool big) { return big ? 32 : batch_lanes(n); }
+__host__ __device__ constexpr uint64_t geo_chunk_cw(uint32_t n, bool big)
+{
+    return (uint64_t)geo_G(n, big) * (uint64_t)geo_lanes(n, big);
+}
+__host__ __device__ constexpr int geo_chunks(uint32_t n, bool big) { return big && n == 127 ? 2 : batch_chunks(n); }
+
 uint64_t packet_tiles(uint32_t n, uint64_t num_codewords)
 {
     const uint64_t chunk = batch_chunk_cw(n);
@@ -85,10 +101,11 @@ struct PacketView {
 // latency-bound tails overlap the streaming of full tiles instead of running
 // as a phase of their own.  view(i) describes packet i; emit(tile) takes a tile.
 template <class View, class Emit>
-void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit)
+void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit, bool big = false)
 {
-    const uint64_t chunk = batch_chunk_cw(n);
-    const uint64_t per = (uint64_t)batch_chunks(n);
+    big = big && big_geometry(n);
+    const uint64_t chunk = geo_chunk_cw(n, big);
+    const uint64_t per = (uint64_t)geo_chunks(n, big);
     auto nfull_of = [&](const PacketView &p) { return n == 3 ? 0 : p.num_cw / chunk; };  // n = 3: all tail
     uint64_t nf = 0, nt = 0;  // full tiles and tail tiles of this n
     for (uint32_t i = 0; i < num_packets; ++i) {
@@ -138,18 +155,20 @@ void emit_code_tiles(uint32_t n, uint32_t num_packets, View view, Emit emit)
 // n = 31: 3968; n = 15, two chunks: 3840; n = 7, four: 3584) plus a spare
 // group for the funnel read; 4 KB stages let 16 one-warp CTAs share an SM.
 constexpr uint32_t kBatchStageBytes = 4096 + 16;
+constexpr uint32_t kBigStageBytes = 8192 + 16;  // the split configuration's long codes
 // Full tiles write their syndromes straight to global memory (each lane's run
 // of G syndromes is contiguous); only a ragged tail, at most one chunk, stages
 // them here before the copy that keeps within the packet.
 constexpr uint32_t kBatchSynBytes = 32 * 32 * 2;  // one chunk of at most 1024 codewords, u16
 
-template <int WARPS, int S, bool T15>
+template <int WARPS, int S, bool T15, bool BIG = false>
 struct BatchCfg {
+    static constexpr uint32_t stage_bytes = BIG ? kBigStageBytes : kBatchStageBytes;
     static constexpr uint32_t off_bar = 0;
     static constexpr uint32_t off_claim = 64;  // per stage: the claimed tile index and its descriptor
     static constexpr uint32_t off_desc = 128;
     static constexpr uint32_t off_stage = off_desc + 8 * 64;
-    static constexpr uint32_t off_syn = off_stage + S * kBatchStageBytes;
+    static constexpr uint32_t off_syn = off_stage + S * stage_bytes;
     static constexpr uint32_t warp_bytes = (off_syn + kBatchSynBytes + 127) / 128 * 128;
     // behind the warps' areas: the n = 7 decode table, (T15) the n = 15 one,
     // and the mbarrier of the n = 15 table's bulk copies
@@ -168,45 +187,51 @@ struct BatchCfg {
 // chunk's input because k < n.  Chunk c's syndromes go to sdst + c * (bytes of
 // one chunk's syndromes): global memory for a full tile, the warp's staging
 // buffer for a tail.
-template <int N_, int SYN, bool LUT>
+template <int N_, int SYN, bool LUT, bool BIG = false>
 __device__ __forceinline__ uint32_t batch_chunk(const uint32_t *stage, uint8_t *sdst, int lane, uint32_t chunks,
                                                 const uint16_t *lut)
 {
-    using Q = ChunkGeom<N_, SYN, batch_G(N_), false, batch_lanes(N_)>;
+    constexpr bool B = BIG && big_geometry(N_);
+    constexpr int G = geo_G(N_, B), LN = geo_lanes(N_, B);
+    using Q = ChunkGeom<N_, SYN, G, false, LN>;
     uint32_t e = 0, unused = 0;
     for (uint32_t c = 0; c < chunks; ++c)
-        e += decode_warp_chunk<N_, SYN, batch_G(N_), false, LUT, batch_lanes(N_)>(stage + c * Q::in_words,
-                                                                  const_cast<uint32_t *>(stage) + c * Q::out_words,
-                                                                  sdst + c * Q::syn_bytes, lane, unused, lut);
+        e += decode_warp_chunk<N_, SYN, G, false, LUT, LN>(stage + c * Q::in_words,
+                                                           const_cast<uint32_t *>(stage) + c * Q::out_words,
+                                                           sdst + c * Q::syn_bytes, lane, unused, lut);
     return e;
 }
 
 // LUT: decode with the table `lut` in shared memory (n = 7 and 15 only).
-template <int N_, bool LUT = false>
+template <int N_, bool LUT = false, bool BIG = false>
 __device__ __forceinline__ uint32_t batch_chunk_syn(uint32_t syn_type, const uint32_t *stage, uint8_t *sdst, int lane,
                                                     uint32_t chunks, const uint16_t *lut = nullptr)
 {
     switch (syn_type) {
-        case 1: return batch_chunk<N_, 1, LUT>(stage, sdst, lane, chunks, lut);
-        case 2: return batch_chunk<N_, 2, LUT>(stage, sdst, lane, chunks, lut);
-        default: return batch_chunk<N_, 0, LUT>(stage, sdst, lane, chunks, lut);
+        case 1: return batch_chunk<N_, 1, LUT, BIG>(stage, sdst, lane, chunks, lut);
+        case 2: return batch_chunk<N_, 2, LUT, BIG>(stage, sdst, lane, chunks, lut);
+        default: return batch_chunk<N_, 0, LUT, BIG>(stage, sdst, lane, chunks, lut);
     }
 }
 
-__device__ __forceinline__ uint32_t chunk_codewords(uint32_t n) { return (uint32_t)batch_chunk_cw(n); }
+__device__ __forceinline__ uint32_t chunk_codewords(uint32_t n, bool big = false)
+{
+    return (uint32_t)geo_chunk_cw(n, big && big_geometry(n));
+}
 
 // lut7 (or nullptr: arithmetic decode) and, with T15, lut15 (required) are
 // the global decode tables of n = 7 and 15; the kernel copies them into shared
 // memory once per CTA.  NSEL = 0 decodes tiles of every n; NSEL = n compiles
 // only the decoder of that n (every tile of the table must be of that n), so
 // that the kernel's code fits the instruction cache.
-template <int WARPS, int S, bool T15, int NSEL = 0>
+template <int WARPS, int S, bool T15, int NSEL = 0, bool BIG = false>
 __global__ void __launch_bounds__(WARPS * 32)
     k_decode_batch(const DevTile *__restrict__ tiles, uint32_t num_tiles, uint32_t *__restrict__ counter,
                    unsigned long long *__restrict__ err_counts, uint32_t *__restrict__ status,
                    const uint16_t *__restrict__ lut7, const uint16_t *__restrict__ lut15)
 {
-    using Cfg = BatchCfg<WARPS, S, T15>;
+    using Cfg = BatchCfg<WARPS, S, T15, BIG>;
+    static_assert(!BIG || big_geometry(NSEL), "the 8 KB geometry is for the long codes' single-n kernels");
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *lut_bar = reinterpret_cast<uint64_t *>(smem + Cfg::off_lut_bar);
@@ -242,7 +267,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (t < num_tiles) desc[s] = d;
         if (t < num_tiles && d.bytes != 0) {
             mbar_arrive_expect_tx(&bar[s], d.bytes);
-            bulk_g2s(s_stage + s * kBatchStageBytes, d.in + d.c0 * d.n / 32u, d.bytes, &bar[s]);
+            bulk_g2s(s_stage + s * Cfg::stage_bytes, d.in + d.c0 * d.n / 32u, d.bytes, &bar[s]);
         } else {
             mbar_arrive(&bar[s]);
         }
@@ -327,14 +352,14 @@ __global__ void __launch_bounds__(WARPS * 32)
         } p{tl.in, tl.out, tl.syn, tl.num_cw, (tl.num_cw * tl.n + 31) / 32, (tl.num_cw * (tl.n - tl.m) + 31) / 32,
             tl.n, tl.m, tl.syn_type};
         const bool full = (tl.count & kFullTile) != 0;
-        const uint32_t chunks = full ? (tl.count & ~kFullTile) / chunk_codewords(p.n) : 0u;
-        uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * kBatchStageBytes);
+        const uint32_t chunks = full ? (tl.count & ~kFullTile) / chunk_codewords(p.n, BIG) : 0u;
+        uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * Cfg::stage_bytes);
         uint8_t *sbuf = s_syn;
         uint8_t *sdst = (full && p.syn_type != 0) ? p.syn + tl.c0 * (p.syn_type == 2 ? 2u : 1u) : sbuf;
         unsigned long long errs = 0;
         const bool chunked = NSEL == 0 ? (full || p.n != 3) : NSEL != 3;  // n = 3 tiles are all tails
         if (chunked) {
-            const uint32_t cwords = chunk_codewords(p.n);
+            const uint32_t cwords = chunk_codewords(p.n, BIG);
             const uint32_t k = p.n - p.m;
             const uint32_t cnt = tl.count & ~kFullTile;
             if (!full) {
@@ -383,7 +408,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 else
                     e = batch_chunk_syn<15>(p.syn_type, stage, sdst, lane, nch);
             } else if constexpr (NSEL != 3) {
-                e = batch_chunk_syn<NSEL>(p.syn_type, stage, sdst, lane, nch);
+                e = batch_chunk_syn<NSEL, false, BIG>(p.syn_type, stage, sdst, lane, nch);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
@@ -459,14 +484,14 @@ struct BatchVariant {
                    unsigned long long *, uint32_t *, const uint16_t *, const uint16_t *, bool pdl);
 };
 
-template <int W, int S, bool T15, int NSEL = 0>
+template <int W, int S, bool T15, int NSEL = 0, bool BIG = false>
 void launch_batch_kernel(int grid, uint32_t smem, cudaStream_t st, const DevTile *tiles, uint32_t num_tiles,
                          uint32_t *counter, unsigned long long *err, uint32_t *status, const uint16_t *lut7,
                          const uint16_t *lut15, bool pdl)
 {
     // the callers count batch launches (a plan's once per graph replay)
-    (void)launch_kernel_uncounted(k_decode_batch<W, S, T15, NSEL>, dim3((unsigned)grid), dim3(W * 32), smem, st, pdl,
-                                  tiles, num_tiles, counter, err, status, lut7, lut15);
+    (void)launch_kernel_uncounted(k_decode_batch<W, S, T15, NSEL, BIG>, dim3((unsigned)grid), dim3(W * 32), smem, st,
+                                  pdl, tiles, num_tiles, counter, err, status, lut7, lut15);
 }
 
 // Clears a plan's claim counters and error counters, then lets the next
@@ -480,16 +505,16 @@ __global__ void k_clear_plan(uint32_t *counters, uint32_t num_counters, unsigned
         for (uint32_t j = i; j < num_err; j += stride) err[j] = 0ull;
 }
 
-template <int W, int S, bool T15 = false, int NSEL = 0>
+template <int W, int S, bool T15 = false, int NSEL = 0, bool BIG = false>
 BatchVariant make_batch_variant()
 {
     BatchVariant v;
     v.warps = W;
     v.stages = S;
     v.t15 = T15;
-    v.smem = BatchCfg<W, S, T15>::smem;
-    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S, T15, NSEL>);
-    v.launch = &launch_batch_kernel<W, S, T15, NSEL>;
+    v.smem = BatchCfg<W, S, T15, BIG>::smem;
+    v.kernel = reinterpret_cast<const void *>(k_decode_batch<W, S, T15, NSEL, BIG>);
+    v.launch = &launch_batch_kernel<W, S, T15, NSEL, BIG>;
     return v;
 }
 
@@ -509,9 +534,9 @@ template <int W, int S>
 SplitKernels make_split_kernels()
 {
     SplitKernels s;
-    s.group[0] = make_batch_variant<W, S, false, 255>();
-    s.group[1] = make_batch_variant<W, S, false, 127>();
-    s.group[2] = make_batch_variant<W, S, false, 63>();
+    s.group[0] = make_batch_variant<W, S, false, 255, true>();
+    s.group[1] = make_batch_variant<W, S, false, 127, true>();
+    s.group[2] = make_batch_variant<W, S, false, 63, true>();
     s.group[3] = make_batch_variant<W, S, false, 31>();
     s.group[4] = make_batch_variant<W, S, false, 15>();
     s.group[5] = make_batch_variant<W, S, false, 7>();
@@ -565,6 +590,7 @@ struct hd_plan {
     // the split configuration: each code group's tile range (tiles are grouped
     // by n in kSplitOrder), a stream per group and the fork/join events
     uint32_t grp_begin[kSplitGroups] = {}, grp_end[kSplitGroups] = {};
+    DevTile *d_split = nullptr;  // the split configuration's own tile table (8 KB tiles for the long codes)
     cudaStream_t gstream[kSplitGroups] = {};
     cudaEvent_t fork = nullptr, join[kSplitGroups] = {};
 };
@@ -575,7 +601,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 // Validate the table and build the packet and tile arrays.
 hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector<DevPacket> &pk,
-                       std::vector<DevTile> &tiles, hd_plan *stats)
+                       std::vector<DevTile> &tiles, hd_plan *stats, std::vector<DevTile> *split = nullptr)
 {
     if (num_packets > 0 && table == nullptr) return HD_ERR_NULL;
     pk.resize(num_packets);
@@ -630,6 +656,23 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
         if (stats) stats->grp_end[gi] = (uint32_t)tiles.size();
     }
     if (stats) stats->full_tiles = nfull_tiles;
+    if (split) {
+        // the split configuration's table: the same order, the long codes cut
+        // with the 8 KB geometry; its group ranges replace the ones above
+        split->clear();
+        for (int gi = 0; gi < kSplitGroups; ++gi) {
+            if (stats) stats->grp_begin[gi] = (uint32_t)split->size();
+            emit_code_tiles(
+                kSplitOrder[gi], num_packets,
+                [&](uint32_t i) {
+                    const DevPacket &d = pk[i];
+                    return PacketView{d.in, d.out, d.syn, d.num_cw, d.n, d.m, d.syn_type};
+                },
+                [&](const DevTile &t) { split->push_back(t); }, true);
+            if (stats) stats->grp_end[gi] = (uint32_t)split->size();
+        }
+        if (split->size() >= 0xFFFFFFF0ull) return HD_ERR_CAPACITY;
+    }
     return HD_OK;
 }
 
@@ -714,7 +757,7 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
             cudaStream_t gs = p->gstream[gi];
             if ((e = cudaStreamWaitEvent(gs, p->fork, 0)) != cudaSuccess) return e;
             const BatchVariant &v = *g.gk[gi];
-            v.launch(g.ggrid[gi], v.smem, gs, p->d_tiles + p->grp_begin[gi], p->grp_end[gi] - p->grp_begin[gi],
+            v.launch(g.ggrid[gi], v.smem, gs, p->d_split + p->grp_begin[gi], p->grp_end[gi] - p->grp_begin[gi],
                      p->d_counter + gi, err_counts, status, g.lut7, g.lut15, false);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = cudaEventRecord(p->join[gi], gs)) != cudaSuccess) return e;
@@ -788,8 +831,8 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     hd_plan *p = new (std::nothrow) hd_plan();
     if (!p) return HD_ERR_CAPACITY;
     std::vector<DevPacket> pk;
-    std::vector<DevTile> tiles;
-    hd_status rc = build_tables(table, num_packets, pk, tiles, p);
+    std::vector<DevTile> tiles, split;
+    hd_status rc = build_tables(table, num_packets, pk, tiles, p, &split);
     if (rc != HD_OK) {
         delete p;
         return rc;
@@ -798,13 +841,17 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     p->num_packets = num_packets;
     p->num_tiles = (uint32_t)tiles.size();
     const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
-    if (cudaMalloc(&p->dmem, tl_b + 256) != cudaSuccess) {
+    const size_t sp_b = (split.size() * sizeof(DevTile) + 255) / 256 * 256;
+    if (cudaMalloc(&p->dmem, tl_b + 256 + sp_b) != cudaSuccess) {
         delete p;
         return HD_ERR_CUDA;
     }
     p->d_tiles = static_cast<DevTile *>(p->dmem);
     p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + tl_b);
+    p->d_split = reinterpret_cast<DevTile *>(static_cast<char *>(p->dmem) + tl_b + 256);
     bool ok = (tiles.empty() || cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
+                                           cudaMemcpyHostToDevice) == cudaSuccess) &&
+              (split.empty() || cudaMemcpy(p->d_split, split.data(), split.size() * sizeof(DevTile),
                                            cudaMemcpyHostToDevice) == cudaSuccess) &&
               cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
