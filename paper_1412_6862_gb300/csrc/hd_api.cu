@@ -37,10 +37,14 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 namespace {
 
-// Lets the next kernel of the stream launch at once, then clears the counters.
+// Lets the next kernel of the stream launch at once, waits for the kernel
+// ahead of it (when it was launched as its programmatic dependent, that
+// kernel may still be running and adding to these very counters), then
+// clears the counters.
 __global__ void k_zero_counts(unsigned long long *a, unsigned long long *b)
 {
     grid_dep_launch_dependents();
+    grid_dep_wait();
     if (threadIdx.x == 0) {
         if (a) *a = 0ull;
         if (b) *b = 0ull;
@@ -112,11 +116,9 @@ hd_status enqueue_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, u
 
 }  // namespace
 
-cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st)
+cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st, bool chained)
 {
-    k_zero_counts<<<1, 32, 0, st>>>(a, b);
-    count_launch();
-    return cudaGetLastError();
+    return launch_kernel(k_zero_counts, dim3(1), dim3(32), 0, st, chained, a, b);
 }
 
 }  // namespace hd
@@ -172,9 +174,11 @@ hd_status hd_decode(const uint32_t *stream, uint64_t in_bits, uint32_t n, uint64
         if (err_count && cudaMemsetAsync(err_count, 0, sizeof(*err_count), st) != cudaSuccess) return HD_ERR_CUDA;
         return HD_OK;
     }
-    if (err_count && launch_zero_counts(err_count, nullptr, st) != cudaSuccess) return HD_ERR_CUDA;
-    return enqueue_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, st,
-                          err_count != nullptr);
+    // the clear and the decode both chained (programmatic dependent launch):
+    // the clear may start while the kernel ahead drains and waits for it
+    // before writing; the decode waits for the clear before touching memory
+    if (err_count && launch_zero_counts(err_count, nullptr, st, true) != cudaSuccess) return HD_ERR_CUDA;
+    return enqueue_decode(stream, in_bits, n, num_codewords, out_bits, syndromes, syn_type, err_count, st, true);
 }
 
 hd_status hd_decode_streams(const hd_stream_job *jobs, uint32_t num_jobs, void *cuda_stream)

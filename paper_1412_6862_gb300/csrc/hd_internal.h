@@ -82,9 +82,13 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 // Clear one or two device counters (either may be NULL) with a one-thread
 // kernel that lets the next kernel of the stream start at once (programmatic
 // dependent launch): a launch with pdl = true below overlaps it and waits for
-// it only before adding to the counters.  Inside a CUDA graph this costs far
-// less than a memset node between two kernels.
-cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st);
+// it before touching global memory.  Inside a CUDA graph this costs far less
+// than a memset node between two kernels.  chained: the clear is itself
+// launched as the programmatic dependent of the kernel ahead of it (it waits
+// for that kernel before writing), so that it and the decode behind it can
+// start while that kernel drains; only for decodes that wait before their
+// first global access.
+cudaError_t launch_zero_counts(unsigned long long *a, unsigned long long *b, cudaStream_t st, bool chained = false);
 
 // Specialised streaming decoder.  Decodes the longest prefix of whole chunks
 // it supports and returns the number of codewords covered in *covered (0 when

@@ -161,13 +161,13 @@ hd_status hd_decode_secded(const uint32_t *stream, uint64_t in_bits, uint32_t n,
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const bool counted = err_count != nullptr || detected_count != nullptr;
-    if (counted && launch_zero_counts(err_count, detected_count, st) != cudaSuccess) return HD_ERR_CUDA;
+    if (counted && launch_zero_counts(err_count, detected_count, st, true) != cudaSuccess) return HD_ERR_CUDA;
     if (num_codewords == 0) return HD_OK;
     const uint32_t k = n - (uint32_t)m;
     const int syn = syndromes ? (int)syn_type : 0;
     uint64_t covered = 0;
     if (launch_decode_fast_secded(stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count, st,
-                                  &covered, counted) != cudaSuccess)
+                                  &covered, true) != cudaSuccess)
         return HD_ERR_CUDA;
     if (covered < num_codewords) {
         const uint64_t tiles = (num_codewords + 31) / 32 - covered / 32;

@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(T)
     using Cfg = StreamCfg<N_, SYN, T, S, G, INPLACE, XH, LUT>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Programmatic dependent launch, both ways: the next kernel of the stream
+    // may launch now (an hd_decode behind this one starts its launch and
+    // prologue while this one drains), and this kernel may have started before
+    // the kernel ahead of it finished, so it touches no global memory other
+    // than the library's own decode table before grid_dep_wait() below.
+    grid_dep_launch_dependents();
     uint64_t *lut_bar = nullptr;
     if constexpr (LUT) {
         // the decode table: bulk copies into shared memory behind the warps'
@@ -213,6 +219,7 @@ __global__ void __launch_bounds__(T)
     uint8_t *s_out = wbase + Cfg::off_out;
     const uint64_t gw = (uint64_t)blockIdx.x * Cfg::WARPS + warp;  // global warp index
     const uint64_t tw = (uint64_t)gridDim.x * Cfg::WARPS;          // warps in the grid
+    grid_dep_wait();  // the kernels ahead (the counters' clear, and what produced the input) have finished
 
     if constexpr (!Cfg::PADDED) {
         if (lane == 0) {
@@ -342,7 +349,6 @@ __global__ void __launch_bounds__(T)
         for (int o = 16; o > 0; o >>= 1) dets += __shfl_xor_sync(0xFFFFFFFFu, dets, o);
     }
     if (lane == 0) {
-        grid_dep_wait();
         if (err != nullptr && errs != 0) atomicAdd(err, (unsigned long long)errs);
         if (XH && det != nullptr && dets != 0) atomicAdd(det, (unsigned long long)dets);
     }
@@ -370,8 +376,9 @@ cudaError_t launch_stream_variant(const StreamVariant &v, const uint32_t *in, ui
     const uint64_t cap = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t want = (nchunks + Cfg::WARPS - 1) / Cfg::WARPS;
     const int grid = decode_grid(want, cap);
-    // with pdl the launch may overlap the counters' clear ahead of it; the
-    // kernel waits for that clear before it counts
+    // with pdl the launch may overlap the kernel ahead of it (the counters'
+    // clear, or a decode's drain); the kernel waits for it before its first
+    // access to global memory
     return launch_kernel(kern, dim3((unsigned)grid), dim3(T), Cfg::smem, st, pdl, in, out,
                          static_cast<uint8_t *>(syn), err, status, nchunks, det, lut);
 }
