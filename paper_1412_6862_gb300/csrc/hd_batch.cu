@@ -541,7 +541,7 @@ SplitKernels make_split_kernels()
     s.group[4] = make_batch_variant<W, S, false, 15>();
     s.group[5] = make_batch_variant<W, S, false, 7>();
     s.group[6] = make_batch_variant<W, S, false, 3>();
-    s.n15_table = make_batch_variant<12, 2, true, 15>();
+    s.n15_table = make_batch_variant<14, 2, true, 15>();
     return s;
 }
 
