@@ -62,19 +62,16 @@ __host__ __device__ constexpr uint64_t batch_chunk_cw(uint32_t n)
 // and load latency are amortised.
 __host__ __device__ constexpr int batch_chunks(uint32_t n) { return n <= 7 ? 4 : (n <= 15 ? 2 : 1); }
 
-// The split configuration's geometry (BIG) for every code but n = 3 (all
-// tails) and n = 15 (whose kernel holds the 64 KB table beside its warps): the
-// streaming kernel's chunk shapes in 8 KB stages -- n = 7 with eight
-// 1024-codeword chunks per tile (7168 bytes), n = 31 with two (7936 bytes),
-// n = 63 with 32 codewords per thread (1024 per chunk, 8064 bytes), n = 127
-// with two 256-codeword chunks (8128 bytes), n = 255 with full-warp chunks of
-// 256 codewords (8160 bytes) -- so that a tile holds about twice the work of
-// the 4 KB tiles, and n = 63 and 255 decode whole 32-codeword tiles per thread
-// part.
-__host__ __device__ constexpr bool big_geometry(uint32_t n)
-{
-    return n == 7 || n == 31 || n == 63 || n == 127 || n == 255;
-}
+// The long codes' geometry in the split configuration (BIG): the streaming
+// kernel's chunk shapes in 8 KB stages -- n = 63 with 32 codewords per thread
+// (1024 per chunk, 8064 bytes), n = 127 with two 256-codeword chunks per tile
+// (8128 bytes), n = 255 with full-warp chunks of 256 codewords (8160 bytes) --
+// so that a tile holds twice the work of the 4 KB tiles, and n = 63 and 255
+// decode whole 32-codeword tiles per thread part (n = 255: 0.42 -> 0.57 of
+// the HBM peak on its share of the batched workload).  The same 8 KB tiles
+// measured no faster for n = 7 and 31, and n = 15's kernel holds its 64 KB
+// table beside its warps, so the other codes keep the 4 KB geometry.
+__host__ __device__ constexpr bool big_geometry(uint32_t n) { return n == 63 || n == 127 || n == 255; }
 __host__ __device__ constexpr int geo_G(uint32_t n, bool big) { return big && n == 63 ? 32 : batch_G(n); }
 __host__ __device__ constexpr int geo_lanes(uint32_t n, bool big) { return big ? 32 : batch_lanes(n); }
 __host__ __device__ constexpr uint64_t geo_chunk_cw(uint32_t n, bool big)
@@ -83,7 +80,7 @@ __host__ __device__ constexpr uint64_t geo_chunk_cw(uint32_t n, bool big)
 }
 __host__ __device__ constexpr int geo_chunks(uint32_t n, bool big)
 {
-    return !big ? batch_chunks(n) : (n == 7 ? 8 : (n == 31 || n == 127) ? 2 : 1);
+    return !big ? batch_chunks(n) : (n == 127 ? 2 : 1);
 }
 
 uint64_t packet_tiles(uint32_t n, uint64_t num_codewords)
@@ -351,14 +348,18 @@ __global__ void __launch_bounds__(WARPS * 32)
             later_t = deal();  // its descriptor is fetched next iteration
         }
         const DevTile tl = desc[s];  // written by lane 0 before the stage's arrive
+        // the single-n kernels know n at compile time: the per-tile index
+        // arithmetic (word counts, chunks per tile) folds to constants
+        const uint32_t pn = NSEL != 0 ? (uint32_t)NSEL : (uint32_t)tl.n;
+        const uint32_t pm = NSEL != 0 ? (uint32_t)log2_exact(NSEL + 1) : (uint32_t)tl.m;
         struct {
             const uint32_t *in;
             uint32_t *out;
             uint8_t *syn;
             uint64_t num_cw, in_words, out_words;
             uint32_t n, m, syn_type;
-        } p{tl.in, tl.out, tl.syn, tl.num_cw, (tl.num_cw * tl.n + 31) / 32, (tl.num_cw * (tl.n - tl.m) + 31) / 32,
-            tl.n, tl.m, tl.syn_type};
+        } p{tl.in, tl.out, tl.syn, tl.num_cw, (tl.num_cw * pn + 31) / 32, (tl.num_cw * (pn - pm) + 31) / 32,
+            pn, pm, tl.syn_type};
         const bool full = (tl.count & kFullTile) != 0;
         const uint32_t chunks = full ? (tl.count & ~kFullTile) / chunk_codewords(p.n, BIG) : 0u;
         uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage + s * Cfg::stage_bytes);
@@ -545,9 +546,9 @@ SplitKernels make_split_kernels()
     s.group[0] = make_batch_variant<W, S, false, 255, true>();
     s.group[1] = make_batch_variant<W, S, false, 127, true>();
     s.group[2] = make_batch_variant<W, S, false, 63, true>();
-    s.group[3] = make_batch_variant<W, S, false, 31, true>();
+    s.group[3] = make_batch_variant<W, S, false, 31>();
     s.group[4] = make_batch_variant<W, S, false, 15>();
-    s.group[5] = make_batch_variant<W, S, false, 7, true>();
+    s.group[5] = make_batch_variant<W, S, false, 7>();
     s.group[6] = make_batch_variant<W, S, false, 3>();
     s.n15_table = make_batch_variant<14, 2, true, 15>();
     return s;
