@@ -391,9 +391,11 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
  * n = 7 arithmetically). */
 hd_status hd_plan_launch(hd_plan *plan, unsigned long long *err_counts, void *cuda_stream);
 
-/* Time every batch-kernel configuration on the plan's own packets (`reps`
- * launches each, 0 = 3; output buffers are overwritten, inputs only read),
- * keep the fastest and report it.  Synchronises the stream. */
+/* Time every batch-kernel configuration on the plan's own packets as
+ * hd_plan_launch() runs it (recorded as a CUDA graph, then `reps` replays,
+ * 0 = 3; output buffers are overwritten, inputs only read), keep the fastest
+ * and report it.  The next hd_plan_launch() records its graph anew.
+ * Synchronises the stream. */
 hd_status hd_plan_autotune(hd_plan *plan, uint32_t reps, void *cuda_stream, hd_plan_info *chosen);
 
 /* Pin batch-kernel configuration `variant` (< hd_plan_info.num_variants). */

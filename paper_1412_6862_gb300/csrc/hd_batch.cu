@@ -917,19 +917,20 @@ hd_status hd_plan_autotune(hd_plan *p, uint32_t reps, void *cuda_stream, hd_plan
     float best_us = 0.f;
     const int keep = p->variant;
     hd_status rc = HD_OK;
+    // every configuration timed as hd_plan_launch runs it: recorded as a CUDA
+    // graph, then replayed (err_counts NULL: the counts are not part of the choice)
     for (int i = 0; i < plan_variants(); ++i) {
         p->variant = i;
         LaunchGeom geom;
-        if (prepare_plan(p, &geom, st) != cudaSuccess || geom.variant != (int)i) continue;
-        if (enqueue_plan(p, geom, nullptr, st) != cudaSuccess) {
-            rc = HD_ERR_CUDA;
-            break;
-        }
+        if (prepare_plan(p, &geom, st) != cudaSuccess || geom.variant != i) continue;
+        drop_graph(p);
+        if ((rc = hd_plan_launch(p, nullptr, st)) != HD_OK) break;  // records the graph and runs it once
         cudaEventRecord(e0, st);
-        for (uint32_t r = 0; r < reps; ++r) enqueue_plan(p, geom, nullptr, st);
+        for (uint32_t r = 0; r < reps; ++r)
+            if ((rc = hd_plan_launch(p, nullptr, st)) != HD_OK) break;
         cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = HD_ERR_CUDA;
+        if (rc != HD_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            if (rc == HD_OK) rc = HD_ERR_CUDA;
             break;
         }
         float ms = 0.f;
