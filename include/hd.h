@@ -353,16 +353,23 @@ typedef struct {
 typedef struct hd_plan hd_plan;
 
 /* A plan decodes with one of num_variants configurations: variants
- * 0 .. num_variants - 2 launch one persistent kernel that decodes tiles of
- * every n; the last one (the split configuration) launches one kernel per
- * code length present, each compiled for that n alone, as concurrent branches
- * forked from and joined back into the launching stream (its n = 15 kernel
- * holds the n = 15 decode table once that is filled). */
+ * 0 .. num_variants - 3 launch one persistent kernel that decodes tiles of
+ * every n; variant num_variants - 2 (the split configuration) launches one
+ * kernel per code length present, each compiled for that n alone, as
+ * concurrent branches forked from and joined back into the launching stream
+ * (its n = 15 kernel holds the n = 15 decode table once that is filled); the
+ * last one (the stream-group configuration) runs the streaming decoder's
+ * chunk geometry over each (n, syndrome type) group of packets, one
+ * concurrent branch per group, each warp decoding an equal contiguous share
+ * of the group's whole chunks and ragged tails (n = 3 packets go to the tile
+ * kernel in a branch of their own; with 2^22 - 1 packets or more this
+ * configuration gives way to variant 0). */
 typedef struct {
     uint32_t num_packets;
     uint32_t num_tiles;     /* warp work items: full chunks plus ragged tails */
     uint32_t full_tiles;
-    uint32_t warps_per_cta; /* batch-kernel configuration in use (split: that of the kernels without a table) */
+    uint32_t warps_per_cta; /* batch-kernel configuration in use (split: that of the kernels without a table;
+                               stream groups: the longest code's kernel) */
     uint32_t stages;
     uint32_t smem_bytes;
     uint32_t variant;       /* index of the configuration, < num_variants */

@@ -24,6 +24,7 @@
 #include "hd_batch_internal.h"
 #include "hd_generic.cuh"
 #include "hd_internal.h"
+#include "hd_multi.cuh"
 #include "hd_stream.cuh"
 
 namespace hd {
@@ -574,6 +575,43 @@ const std::vector<SplitKernels> &split_kernels()
     static const std::vector<SplitKernels> k = {make_split_kernels<1, 3>()};
     return k;
 }
+
+// The stream-group configuration's kernels (hd_multi_a.cu, hd_multi_b.cu):
+// the streaming decoder over the whole chunks of many packets of one n.
+const std::vector<MultiVariant> &multi_variants()
+{
+    static const std::vector<MultiVariant> v = [] {
+        std::vector<MultiVariant> r;
+        register_multi_a(r);
+        register_multi_b(r);
+        return r;
+    }();
+    return v;
+}
+
+// The kernel of group (n, syn): the one holding the decode table when `lut`
+// and one is compiled, else one without a table (nullptr: n has none).
+const MultiVariant *multi_for(uint32_t n, int syn, bool lut)
+{
+    const MultiVariant *plain = nullptr;
+    for (const MultiVariant &v : multi_variants()) {
+        if (v.n != n || v.syn != syn) continue;
+        if (lut && v.lut) return &v;
+        if (!v.lut && !plain) plain = &v;
+    }
+    return plain;
+}
+
+// Codewords per item of code n in the stream-group configuration (every
+// kernel of one n, with or without a table, uses the same chunk); 0: none.
+uint64_t multi_chunk_cw(uint32_t n)
+{
+    const MultiVariant *v = multi_for(n, 0, false);
+    return v ? v->chunk_cw : 0;
+}
+
+// Groups of the stream-group configuration: (n, syndrome type) pairs.
+constexpr int kMaxGroups = 18;
 }  // namespace hd
 
 using namespace hd;
@@ -602,6 +640,21 @@ struct hd_plan {
     DevTile *d_split = nullptr;  // the split configuration's own tile table (8 KB tiles for the long codes)
     cudaStream_t gstream[kSplitGroups] = {};
     cudaEvent_t fork = nullptr, join[kSplitGroups] = {};
+    // the stream-group configuration: one k_decode_multi launch per (n,
+    // syndrome type) group over its runs of whole chunks, and one batch-kernel
+    // launch over the tiles of the n = 3 packets
+    struct Group {
+        uint32_t n;
+        int syn;
+        uint32_t run_begin, num_runs, nitems;
+    };
+    std::vector<Group> groups;
+    bool groups_ok = false;  // the configuration is available for this plan
+    MultiRun *d_runs = nullptr;
+    DevTile *d_rest = nullptr;
+    uint32_t num_rest = 0;
+    cudaStream_t mstream[kMaxGroups + 1] = {};  // [0]: the n = 3 tiles; [1 + g]: group g
+    cudaEvent_t mjoin[kMaxGroups + 1] = {};
 };
 
 namespace {
@@ -685,6 +738,91 @@ hd_status build_tables(const hd_packet *table, uint32_t num_packets, std::vector
     return HD_OK;
 }
 
+// The stream-group configuration's tables.  For each (n, syndrome type) group
+// (long codes first): the packets' whole chunks, in the streaming kernel's
+// chunk geometry and in packet order, with the packets' ragged tails spread
+// evenly among them (a tail costs more than a chunk -- a plain load of its
+// last words, a zero-filled chunk, a word-by-word copy out -- and each warp
+// decodes a contiguous range of items, so tails grouped together would load
+// a few warps with most of them).  A record describes consecutive chunks of
+// one packet up to the next tail, or one tail (kTailItems items: the first
+// decodes it, the others are padding).  n = 3 packets (no streaming kernel)
+// are cut into batch tiles.  With 2^22 - 1 packets or more (the records'
+// packet field) the configuration is not available.
+hd_status build_group_tables(const std::vector<DevPacket> &pk, std::vector<MultiRun> &runs,
+                             std::vector<DevTile> &rest, std::vector<hd_plan::Group> &groups, bool *available)
+{
+    const uint32_t np = (uint32_t)pk.size();
+    *available = np <= kPacketMask;  // index kPacketMask with the longest tail would read as padding
+    if (!*available) return HD_OK;
+    for (uint32_t n : kSplitOrder) {
+        const uint64_t chunk = multi_chunk_cw(n);
+        if (chunk == 0) continue;
+        for (int syn = 0; syn <= 2; ++syn) {
+            const uint64_t sb = syn == 2 ? 2u : (uint64_t)syn;
+            // record of codewords [c0, ...) of packet i; a chunk fills whole 16-byte
+            // groups of input, output and syndromes, so every record starts aligned
+            auto record = [&](uint32_t i, uint64_t c0, uint32_t c_begin, uint32_t tail) {
+                const DevPacket &d = pk[i];
+                const uint32_t k = d.n - d.m;
+                return MultiRun{d.in + c0 * n / 32u, d.out + c0 * k / 32u, syn != 0 ? d.syn + c0 * sb : nullptr,
+                                c_begin, i | tail << kTailShift};
+            };
+            uint64_t nf = 0, nt = 0;  // whole chunks and tails of the group
+            for (uint32_t i = 0; i < np; ++i) {
+                const DevPacket &d = pk[i];
+                if (d.n != n || (int)d.syn_type != syn) continue;
+                nf += d.num_cw / chunk;
+                nt += (d.num_cw % chunk) != 0;
+            }
+            if (nf + nt == 0) continue;
+            if (nf + nt * kTailItems >= 0xFFFFFFF0ull) return HD_ERR_CAPACITY;
+            hd_plan::Group g{n, syn, (uint32_t)runs.size(), 0u, (uint32_t)(nf + nt * kTailItems)};
+            uint64_t items = 0, done_full = 0, done_tail = 0;
+            uint32_t tp = 0;  // tail cursor: the next packet whose tail may be due
+            auto next_tail = [&]() {
+                for (; tp < np; ++tp) {
+                    const DevPacket &d = pk[tp];
+                    if (d.n != n || (int)d.syn_type != syn || d.num_cw % chunk == 0) continue;
+                    runs.push_back(record(tp, d.num_cw / chunk * chunk, (uint32_t)items, (uint32_t)(d.num_cw % chunk)));
+                    items += kTailItems;
+                    ++done_tail;
+                    ++tp;
+                    return;
+                }
+            };
+            for (uint32_t i = 0; i < np; ++i) {
+                const DevPacket &d = pk[i];
+                if (d.n != n || (int)d.syn_type != syn) continue;
+                const uint64_t whole = d.num_cw / chunk;
+                for (uint64_t j = 0; j < whole;) {
+                    // chunks until the next tail is due: the first x >= 1 with
+                    // (done_full + x) * nt > done_tail * nf
+                    uint64_t x = whole - j;
+                    if (done_tail < nt) x = std::min(x, done_tail * nf / nt + 1 - done_full);
+                    runs.push_back(record(i, j * chunk, (uint32_t)items, 0u));
+                    items += x;
+                    done_full += x;
+                    j += x;
+                    while (done_tail < nt && done_tail * nf < done_full * nt) next_tail();
+                }
+            }
+            while (done_tail < nt) next_tail();
+            g.num_runs = (uint32_t)runs.size() - g.run_begin;
+            groups.push_back(g);
+        }
+    }
+    emit_code_tiles(
+        3, np,
+        [&](uint32_t i) {
+            const DevPacket &d = pk[i];
+            return PacketView{d.in, d.out, d.syn, d.num_cw, d.n, d.m, d.syn_type};
+        },
+        [&](const DevTile &t) { rest.push_back(t); });
+    if (rest.size() >= 0xFFFFFFF0ull) return HD_ERR_CAPACITY;
+    return HD_OK;
+}
+
 int batch_grid(const BatchVariant &v, uint32_t num_tiles)
 {
     const int bps = stream_blocks_per_sm(v.kernel, v.warps * 32, v.smem);
@@ -707,12 +845,18 @@ struct LaunchGeom {
     bool split = false;
     const BatchVariant *gk[kSplitGroups] = {};  // split: the kernel of each code group
     int ggrid[kSplitGroups] = {};
+    bool groups = false;                        // the stream-group configuration
+    const MultiVariant *mk[kMaxGroups] = {};    // its kernel per group
+    int mgrid[kMaxGroups] = {};
+    int rest_grid = 0;                          // the batch kernel's grid for the n = 3 tiles
 };
 
 // Index of the first split configuration among a plan's configurations
-// (after the single-kernel ones), and the number of configurations.
+// (after the single-kernel ones), of the stream-group configuration (the
+// last), and the number of configurations.
 inline int split_variant() { return (int)batch_variants().size(); }
-inline int plan_variants() { return split_variant() + (int)split_kernels().size(); }
+inline int group_variant() { return split_variant() + (int)split_kernels().size(); }
+inline int plan_variants() { return group_variant() + 1; }
 
 cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
 {
@@ -720,6 +864,30 @@ cudaError_t prepare_plan(hd_plan *p, LaunchGeom *g, cudaStream_t st)
     if (g->status == nullptr) return cudaErrorInvalidSymbol;
     g->variant = p->variant;
     g->lut7 = lut_ptr(7, st);
+    if (g->variant == group_variant() && !p->groups_ok) g->variant = 0;
+    if (g->variant == group_variant()) {
+        g->groups = true;
+        g->lut15 = lut_ptr(15, st);
+        g->grid = 0;
+        if (p->num_rest != 0) {
+            g->rest_grid = batch_grid(batch_variants()[0], p->num_rest);
+            if (g->rest_grid <= 0) return cudaErrorInvalidConfiguration;
+            g->grid += g->rest_grid;
+        }
+        for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+            const hd_plan::Group &gr = p->groups[gi];
+            const bool lut = (gr.n == 7 && g->lut7 != nullptr) || (gr.n == 15 && g->lut15 != nullptr);
+            const MultiVariant *mv = multi_for(gr.n, gr.syn, lut);
+            if (mv == nullptr) return cudaErrorInvalidConfiguration;
+            const int bps = stream_blocks_per_sm(mv->kernel, mv->T, mv->smem);
+            if (bps <= 0) return cudaErrorInvalidConfiguration;
+            const uint32_t warps = (uint32_t)mv->T / 32u;
+            g->mk[gi] = mv;
+            g->mgrid[gi] = decode_grid((gr.nitems + warps - 1) / warps, (uint64_t)num_sms() * (uint64_t)bps);
+            g->grid += g->mgrid[gi];
+        }
+        return cudaSuccess;
+    }
     if (g->variant >= split_variant()) {
         g->split = true;
         g->lut15 = lut_ptr(15, st);
@@ -758,6 +926,40 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (p->num_tiles == 0) return cudaSuccess;
+    if (g.groups) {
+        // the groups, long codes first, and the n = 3 packets' batch kernel,
+        // each a branch forked from `st` and joined back into it
+        if ((e = cudaEventRecord(p->fork, st)) != cudaSuccess) return e;
+        auto join = [&](int b) -> cudaError_t {
+            cudaError_t r = cudaGetLastError();
+            if (r == cudaSuccess) r = cudaEventRecord(p->mjoin[b], p->mstream[b]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(st, p->mjoin[b], 0);
+            return r;
+        };
+        if (p->num_rest != 0) {
+            if ((e = cudaStreamWaitEvent(p->mstream[0], p->fork, 0)) != cudaSuccess) return e;
+            const BatchVariant &v = batch_variants()[0];
+            v.launch(g.rest_grid, v.smem, p->mstream[0], p->d_rest, p->num_rest, p->d_counter, err_counts, status,
+                     g.lut7, nullptr, false);
+            if ((e = join(0)) != cudaSuccess) return e;
+        }
+        for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+            const hd_plan::Group &gr = p->groups[gi];
+            const MultiVariant &mv = *g.mk[gi];
+            cudaStream_t gs = p->mstream[1 + gi];
+            if ((e = cudaStreamWaitEvent(gs, p->fork, 0)) != cudaSuccess) return e;
+            MultiArgs a;
+            a.runs = p->d_runs + gr.run_begin;
+            a.err = err_counts;
+            a.status = status;
+            a.lut = !mv.lut ? nullptr : (gr.n == 7 ? g.lut7 : g.lut15);
+            a.num_runs = gr.num_runs;
+            a.nitems = gr.nitems;
+            if ((e = mv.launch(g.mgrid[gi], gs, a)) != cudaSuccess) return e;
+            if ((e = join(1 + (int)gi)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (g.split) {
         // the code groups as concurrent branches forked from `st` and joined back into it
         if ((e = cudaEventRecord(p->fork, st)) != cudaSuccess) return e;
@@ -783,6 +985,7 @@ cudaError_t enqueue_plan(hd_plan *p, const LaunchGeom &g, unsigned long long *er
 uint64_t plan_kernels(const hd_plan *p, const LaunchGeom &g)
 {
     if (p->num_tiles == 0) return 1;  // the counters' clear
+    if (g.groups) return 1 + (p->num_rest != 0 ? 1u : 0u) + (uint64_t)p->groups.size();
     if (!g.split) return 2;
     uint64_t c = 1;
     for (int gi = 0; gi < kSplitGroups; ++gi) c += g.gk[gi] != nullptr;
@@ -840,8 +1043,10 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     hd_plan *p = new (std::nothrow) hd_plan();
     if (!p) return HD_ERR_CAPACITY;
     std::vector<DevPacket> pk;
-    std::vector<DevTile> tiles, split;
+    std::vector<DevTile> tiles, split, rest;
+    std::vector<MultiRun> runs;
     hd_status rc = build_tables(table, num_packets, pk, tiles, p, &split);
+    if (rc == HD_OK) rc = build_group_tables(pk, runs, rest, p->groups, &p->groups_ok);
     if (rc != HD_OK) {
         delete p;
         return rc;
@@ -849,24 +1054,35 @@ hd_status hd_plan_create(const hd_packet *table, uint32_t num_packets, hd_plan *
     cudaGetDevice(&p->device);
     p->num_packets = num_packets;
     p->num_tiles = (uint32_t)tiles.size();
-    const size_t tl_b = (tiles.size() * sizeof(DevTile) + 255) / 256 * 256;
-    const size_t sp_b = (split.size() * sizeof(DevTile) + 255) / 256 * 256;
-    if (cudaMalloc(&p->dmem, tl_b + 256 + sp_b) != cudaSuccess) {
+    p->num_rest = (uint32_t)rest.size();
+    auto rounded = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t tl_b = rounded(tiles.size() * sizeof(DevTile)), sp_b = rounded(split.size() * sizeof(DevTile));
+    const size_t ru_b = rounded(runs.size() * sizeof(MultiRun)), re_b = rounded(rest.size() * sizeof(DevTile));
+    if (cudaMalloc(&p->dmem, tl_b + 256 + sp_b + ru_b + re_b) != cudaSuccess) {
         delete p;
         return HD_ERR_CUDA;
     }
-    p->d_tiles = static_cast<DevTile *>(p->dmem);
-    p->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dmem) + tl_b);
-    p->d_split = reinterpret_cast<DevTile *>(static_cast<char *>(p->dmem) + tl_b + 256);
-    bool ok = (tiles.empty() || cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile),
-                                           cudaMemcpyHostToDevice) == cudaSuccess) &&
-              (split.empty() || cudaMemcpy(p->d_split, split.data(), split.size() * sizeof(DevTile),
-                                           cudaMemcpyHostToDevice) == cudaSuccess) &&
+    char *base = static_cast<char *>(p->dmem);
+    p->d_tiles = reinterpret_cast<DevTile *>(base);
+    p->d_counter = reinterpret_cast<uint32_t *>(base + tl_b);
+    p->d_split = reinterpret_cast<DevTile *>(base + tl_b + 256);
+    p->d_runs = reinterpret_cast<MultiRun *>(base + tl_b + 256 + sp_b);
+    p->d_rest = reinterpret_cast<DevTile *>(base + tl_b + 256 + sp_b + ru_b);
+    auto upload = [](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = upload(p->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile)) &&
+              upload(p->d_split, split.data(), split.size() * sizeof(DevTile)) &&
+              upload(p->d_runs, runs.data(), runs.size() * sizeof(MultiRun)) &&
+              upload(p->d_rest, rest.data(), rest.size() * sizeof(DevTile)) &&
               cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int gi = 0; ok && gi < kSplitGroups; ++gi)
         ok = cudaStreamCreateWithFlags(&p->gstream[gi], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&p->join[gi], cudaEventDisableTiming) == cudaSuccess;
+    for (size_t b = 0; ok && b <= p->groups.size(); ++b)
+        ok = cudaStreamCreateWithFlags(&p->mstream[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->mjoin[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         hd_plan_destroy(p);
         return HD_ERR_CUDA;
@@ -955,9 +1171,10 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
 {
     if (!p || !info) return HD_ERR_NULL;
     std::memset(info, 0, sizeof(*info));
-    const bool split = p->variant >= split_variant();
+    const bool groups = p->variant == group_variant();
+    const bool split = p->variant >= split_variant() && !groups;
     const BatchVariant &v = split ? split_kernels()[p->variant - split_variant()].group[0]
-                                  : batch_variants()[p->variant];
+                                  : batch_variants()[groups ? 0 : p->variant];
     info->num_packets = p->num_packets;
     info->num_tiles = p->num_tiles;
     info->full_tiles = p->full_tiles;
@@ -968,10 +1185,19 @@ hd_status hd_plan_get_info(const hd_plan *p, hd_plan_info *info)
     info->warps_per_cta = (uint32_t)v.warps;
     info->stages = (uint32_t)v.stages;
     info->smem_bytes = v.smem;
+    if (groups && !p->groups.empty()) {
+        // the kernel of the first group (the longest code present)
+        const MultiVariant *mv = multi_for(p->groups[0].n, p->groups[0].syn, false);
+        if (mv) {
+            info->warps_per_cta = (uint32_t)mv->T / 32u;
+            info->stages = (uint32_t)mv->S;
+            info->smem_bytes = mv->smem;
+        }
+    }
     info->variant = (uint32_t)p->variant;
     info->num_variants = (uint32_t)plan_variants();
     info->measured_us = p->tuned_us;
-    info->table_lookup = 1u | (v.t15 || split ? 2u : 0u);
+    info->table_lookup = 1u | (v.t15 || split || groups ? 2u : 0u);
     return HD_OK;
 }
 
@@ -992,6 +1218,10 @@ void hd_plan_destroy(hd_plan *p)
     for (int gi = 0; gi < kSplitGroups; ++gi) {
         if (p->gstream[gi]) cudaStreamDestroy(p->gstream[gi]);
         if (p->join[gi]) cudaEventDestroy(p->join[gi]);
+    }
+    for (int b = 0; b <= kMaxGroups; ++b) {
+        if (p->mstream[b]) cudaStreamDestroy(p->mstream[b]);
+        if (p->mjoin[b]) cudaEventDestroy(p->mjoin[b]);
     }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->dmem) cudaFree(p->dmem);

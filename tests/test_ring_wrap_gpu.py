@@ -88,12 +88,14 @@ def _secded_received(n, N, seed):
     return st
 
 
-@pytest.mark.parametrize("n", [7, 15, 31, 63, 127, 255])
-@pytest.mark.parametrize("syn", [hd.SYN_NONE, hd.SYN_U8, hd.SYN_U16])
+# u8 SECDED syndromes hold n <= 127 (s | P << m takes m + 1 bits)
+_SECDED_CASES = [(n, syn) for n in (7, 15, 31, 63, 127, 255) for syn in (hd.SYN_NONE, hd.SYN_U8, hd.SYN_U16)
+                 if not (syn == hd.SYN_U8 and n == 255)]
+
+
+@pytest.mark.parametrize("n,syn", _SECDED_CASES)
 def test_secded_configurations_wrap_their_rings(n, syn):
     import torch
-    if syn == hd.SYN_U8 and n == 255:
-        pytest.skip("u8 SECDED syndromes need n <= 127")
     m, k = hd.code_params(n)
     cnt = hd.hd_secded_variant_count(n, syn)
     assert cnt >= 1
@@ -155,6 +157,48 @@ def test_batch_configurations_wrap_their_rings():
                 check_batch(pkts, exp, err)
             except AssertionError as e:
                 raise AssertionError(f"batch configuration {vi}: {e}") from None
+    finally:
+        plan.close()
+    assert hd.hd_device_status() == 0
+
+
+def test_stream_group_configuration_wraps_its_rings():
+    """The batch plan's stream-group configuration (its last) on two CTAs per
+    kernel: every (n, syndrome type) group holds over 300 whole chunks, so that
+    each warp of the widest group kernel (18 warps) walks at least eight items
+    of its range; packets of one group sit apart in the table and mix lengths
+    of many chunks, one chunk, less than a chunk and none, so that runs, the
+    run window and the rest's tiles are all exercised."""
+    import torch
+    from tests.test_batch_gpu import check_batch
+    groups = [(n, st) for n in (7, 15, 31, 63, 127, 255) for st in (hd.SYN_NONE, hd.SYN_U8, hd.SYN_U16)]
+    # packet lengths in chunks of the group's kernel (1024 codewords up to
+    # n = 63, 256 above): 302 whole chunks per group in all
+    shapes = (lambda c: 100 * c + 17, lambda c: c, lambda c: c - 1, lambda c: 5, lambda c: 60 * c,
+              lambda c: 139 * c + c // 2, lambda c: 0, lambda c: 2 * c + 1)
+    specs = [(n, st, shape(1024 if n <= 63 else 256)) for shape in shapes for n, st in groups]
+    pkts, exp = [], []
+    for j, (n, st, N) in enumerate(specs):
+        stream, _, _ = gc.received_stream(n, N, seed=9100 + j, p1=0.1, p2=0.02)
+        e = gc.expected(stream, n, N, st) if N else (np.zeros(0, np.uint32), None, 0)
+        m, k = hd.code_params(n)
+        out = torch.full((max(1, hd.words_for(N * k)),), -1, dtype=torch.int32, device="cuda")
+        syn = None
+        if st != hd.SYN_NONE:
+            syn = torch.full((max(1, N),), 0x5A, dtype=torch.uint8 if st == 1 else torch.int16, device="cuda")
+        pkts.append((gc.to_device(stream), out, syn, N, n, st))
+        exp.append(e)
+    plan = hd.Plan(pkts)
+    err = torch.full((len(pkts),), 77, dtype=torch.int64, device="cuda")
+    try:
+        info = plan.info()
+        plan.select(info["num_variants"] - 1)
+        for rep in range(2):  # the recorded graph, then its replay
+            for d_in, out, syn, N, n, st in pkts:
+                out.fill_(-1)
+            plan.launch(err)
+            torch.cuda.synchronize()
+            check_batch(pkts, exp, err)
     finally:
         plan.close()
     assert hd.hd_device_status() == 0
