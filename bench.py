@@ -428,6 +428,7 @@ def run_batched(dev, args, peak, keep_pool=False):
         "packets": P, "codewords": int(sum(N for (n, N, *_r) in layout)), "decoded_bits": int(bits),
         "algorithmic_bytes": int(nbytes),
         "persistent_graph": {"gbps": gbps(t_pers), "ms": t_pers * 1e3, "hbm_frac": nbytes / t_pers / 1e9 / peak,
+                             "variant": tuned["variant"], "num_variants": tuned["num_variants"],
                              "warps_per_cta": tuned["warps_per_cta"], "stages": tuned["stages"],
                              "tiles": tuned["num_tiles"]},
         "per_packet_eager": {"gbps": gbps(t_eager), "ms": t_eager * 1e3},

@@ -152,15 +152,26 @@ def test_batched_config_full_size():
     table = hd.packet_table(rows)
     plan = hd.hd_plan_create(table, len(rows))
     err = torch.empty(len(rows), dtype=torch.int64, device="cuda")
-    assert hd.hd_plan_launch(plan, err.data_ptr(), torch.cuda.current_stream().cuda_stream) == hd.HD_OK
-    torch.cuda.synchronize()
-    hd.hd_plan_destroy(plan)
-    o_h = d_out.cpu().numpy().view(np.uint32)
-    s_h = d_syn.cpu().numpy()
-    e_h = err.cpu().numpy()
-    for j, (sp, (s, (eo, es, ee))) in enumerate(zip(specs, made)):
-        m, k = hd.code_params(sp.n)
-        nw = hd.words_for(sp.num_codewords * k)
-        assert np.array_equal(o_h[offs_out[j]:offs_out[j] + nw], eo[:nw]), f"packet {j} (n={sp.n}) data bits"
-        assert np.array_equal(s_h[offs_syn[j]:offs_syn[j] + sp.num_codewords], es), f"packet {j} syndromes"
-        assert e_h[j] == ee, f"packet {j} err_count"
+    try:
+        # every configuration the autotuner can pick, at this size
+        for v in range(hd.hd_plan_get_info(plan)["num_variants"]):
+            hd.hd_plan_select(plan, v)
+            d_out.fill_(-1)
+            d_syn.fill_(0xEE)
+            err.fill_(-1)
+            assert hd.hd_plan_launch(plan, err.data_ptr(), torch.cuda.current_stream().cuda_stream) == hd.HD_OK
+            torch.cuda.synchronize()
+            o_h = d_out.cpu().numpy().view(np.uint32)
+            s_h = d_syn.cpu().numpy()
+            e_h = err.cpu().numpy()
+            for j, (sp, (s, (eo, es, ee))) in enumerate(zip(specs, made)):
+                m, k = hd.code_params(sp.n)
+                nw = hd.words_for(sp.num_codewords * k)
+                assert np.array_equal(o_h[offs_out[j]:offs_out[j] + nw], eo[:nw]), \
+                    f"configuration {v}, packet {j} (n={sp.n}) data bits"
+                assert np.array_equal(s_h[offs_syn[j]:offs_syn[j] + sp.num_codewords], es), \
+                    f"configuration {v}, packet {j} syndromes"
+                assert e_h[j] == ee, f"configuration {v}, packet {j} err_count"
+    finally:
+        hd.hd_plan_destroy(plan)
+    assert hd.hd_device_status() == 0
