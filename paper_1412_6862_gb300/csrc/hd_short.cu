@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
                 const int32_t q0 = (int32_t)(off0 + c * n) - 1 + 32 * (int32_t)tl;  // position 0 is bit -1 of c
                 const uint32_t sh = (uint32_t)q0 & 31u;
                 int32_t wi = q0 >> 5;  // -1 reads the guard word
-                uint32_t cnt = tl < Ym1 ? (Ym1 - 1u - tl) / T + 1u : 0u;  // words before the last one
+                uint32_t cnt = tl < Ym1 ? ((Ym1 - 1u - tl) >> tlog) + 1u : 0u;  // words before the last one
                 uint32_t lo = 0;  // only words of this codeword are read
                 uint32_t ad = st_s + (uint32_t)(wi * 4);
                 if (T == 1) {  // one lane per codeword: each word is the next one's low half
@@ -314,6 +314,22 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
                 uint32_t e[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) e[u] = tp[32 * u];
+                if (w0 - lane >= wlo && w0 - lane + 127 <= whi) {
+                    // all 128 words of this step are the tile's own (warp-uniform): their first
+                    // data bits lie inside the stage, so neither the clamp nor the store test
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t q = sbw + 1024 * u + (int32_t)(e[u] & 0xFFFFu);
+                        const uint32_t lo = st[q >> 5], hi = st[(q >> 5) + 1], sh = (uint32_t)q & 31u;
+                        uint32_t v = __funnelshift_r(lo, hi, sh);
+                        if constexpr (SPLIT) {
+                            const uint32_t m = shl_clamp(1u, e[u] >> 16) - 1u;
+                            v = (v & m) | (__funnelshift_rc(lo, hi, sh + 1u) & ~m);
+                        }
+                        outp[32 * u] = v;
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int32_t q = max(0, min(sbw + 1024 * u + (int32_t)(e[u] & 0xFFFFu), stage_bits));
