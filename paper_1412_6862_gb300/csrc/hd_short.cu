@@ -120,21 +120,6 @@ __device__ __forceinline__ void issue_tile(const ShortArgs &a, uint64_t t, uint8
     if (bytes) bulk_g2s(stage + 16, reinterpret_cast<const uint8_t *>(a.in) + byte0, bytes, bar);
 }
 
-// 32-bit loads from a shared-memory byte address (and the word after it).
-__device__ __forceinline__ uint32_t lds32(uint32_t addr)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-
-__device__ __forceinline__ uint32_t lds32_next(uint32_t addr)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1+4];" : "=r"(v) : "r"(addr));
-    return v;
-}
-
 // The first 32 data bits of the codeword whose position 1 is stage bit cb
 // (positions 3, 5-7, 9-15, 17-31, 33-38).
 __device__ __forceinline__ uint32_t head_word(const uint32_t *st, uint32_t cb)
@@ -208,7 +193,6 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
         }
         uint8_t *stage = wbase + s * Geom::stage_stride;
         uint32_t *st = reinterpret_cast<uint32_t *>(stage + 16);
-        const uint32_t st_s = smem_addr(st);
         uint64_t byte0;
         uint32_t bytes, gcnt;
         tile_span(a, t, byte0, bytes, gcnt);
@@ -235,31 +219,32 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
                 int32_t wi = q0 >> 5;  // -1 reads the guard word
                 uint32_t cnt = tl < Ym1 ? ((Ym1 - 1u - tl) >> tlog) + 1u : 0u;  // words before the last one
                 uint32_t lo = 0;  // only words of this codeword are read
-                uint32_t ad = st_s + (uint32_t)(wi * 4);
+                // plain shared-memory loads, so that the compiler issues the unrolled
+                // iterations' loads ahead of their uses
+                const uint32_t *ad = st + wi;
                 if (T == 1) {  // one lane per codeword: each word is the next one's low half
-                    lo = lds32(ad);
+                    lo = ad[0];
 #pragma unroll 4
                     for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t hi = lds32_next(ad);
-                        ad += 4;
+                        const uint32_t hi = ad[1];
+                        ++ad;
                         const uint32_t y = __funnelshift_r(lo, hi, sh);
                         x ^= y;
                         pm = (pm << 1) | (__popc(y) & 1u);  // bit order reversed below
                         lo = hi;
                     }
                 } else {
-                    const uint32_t step = 4u * T;
 #pragma unroll 4
                     for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t y = __funnelshift_r(lds32(ad), lds32_next(ad), sh);
+                        const uint32_t y = __funnelshift_r(ad[0], ad[1], sh);
                         x ^= y;
                         pm = (pm << 1) | (__popc(y) & 1u);
-                        ad += step;
+                        ad += T;
                     }
-                    if (tl == tl_last) lo = lds32(ad);
+                    if (tl == tl_last) lo = ad[0];
                 }
                 if (tl == tl_last) {  // the last word holds positions up to n only
-                    const uint32_t y = __funnelshift_r(lo, lds32_next(ad), sh) & a.ylast;
+                    const uint32_t y = __funnelshift_r(lo, ad[1], sh) & a.ylast;
                     x ^= y;
                     pm = (pm << 1) | (__popc(y) & 1u);
                     ++cnt;
