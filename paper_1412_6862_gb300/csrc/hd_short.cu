@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
     const uint32_t tlog = a.tlog, T = 1u << tlog, tl = lane & (T - 1u), team = lane >> tlog, G = 32u >> tlog;
     const uint32_t n = a.n, k = a.k, Ym1 = a.Y - 1u;
     const uint32_t tl_last = Ym1 & (T - 1u);
+    const bool wide = ((a.Y + T - 1u) >> tlog) > 32u;  // a lane reads more than 32 words of a codeword
     const int32_t stage_bits = 8 * SB;  // reads past the data stay inside the stage's slack
     uint32_t errs = 0, dets = 0, it = 0;
     bool aborted = false;
@@ -207,17 +208,24 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
             }
         }
 
-        // 1. syndromes.  Lane tl of a team reads position-domain words j = tl + T*i; the low
-        //    syndrome bits come from the XOR of all words, the high bits from the XOR of the
-        //    indices j of the odd-parity words: bit i of pm is the parity of word tl + T*i.
+        // 1. syndromes.  Lane tl of a team reads position-domain words j = tl + T*i (at most
+        //    64); the low syndrome bits come from the XOR of all words, the high bits from the
+        //    XOR of the indices j of the odd-parity words: bit i of pm0 (i < 32) or of pm1
+        //    (i - 32) is the parity of word tl + T*i.
         for (uint32_t cbase = 0; cbase < gcnt; cbase += G) {
             const uint32_t c = cbase + team;
-            uint32_t x = 0, pm = 0;
+            uint32_t x = 0, pm0 = 0, pm1 = 0;
             if (c < gcnt) {
                 const int32_t q0 = (int32_t)(off0 + c * n) - 1 + 32 * (int32_t)tl;  // position 0 is bit -1 of c
                 const uint32_t sh = (uint32_t)q0 & 31u;
                 int32_t wi = q0 >> 5;  // -1 reads the guard word
                 uint32_t cnt = tl < Ym1 ? ((Ym1 - 1u - tl) >> tlog) + 1u : 0u;  // words before the last one
+                const uint32_t n0 = min(cnt, 32u), n1 = cnt - n0;
+                // a word's parity bit is shifted in (bit order reversed below)
+                auto take = [&](uint32_t y, uint32_t &pm) {
+                    x ^= y;
+                    pm = (pm << 1) | (__popc(y) & 1u);
+                };
                 uint32_t lo = 0;  // only words of this codeword are read
                 // plain shared-memory loads, so that the compiler issues the unrolled
                 // iterations' loads ahead of their uses
@@ -225,33 +233,45 @@ __global__ void __launch_bounds__(W * 32) k_short_tiles(ShortArgs a)
                 if (T == 1) {  // one lane per codeword: each word is the next one's low half
                     lo = ad[0];
 #pragma unroll 4
-                    for (uint32_t i = 0; i < cnt; ++i) {
+                    for (uint32_t i = 0; i < n0; ++i, ++ad) {
                         const uint32_t hi = ad[1];
-                        ++ad;
-                        const uint32_t y = __funnelshift_r(lo, hi, sh);
-                        x ^= y;
-                        pm = (pm << 1) | (__popc(y) & 1u);  // bit order reversed below
+                        take(__funnelshift_r(lo, hi, sh), pm0);
+                        lo = hi;
+                    }
+#pragma unroll 4
+                    for (uint32_t i = 0; i < n1; ++i, ++ad) {
+                        const uint32_t hi = ad[1];
+                        take(__funnelshift_r(lo, hi, sh), pm1);
                         lo = hi;
                     }
                 } else {
 #pragma unroll 4
-                    for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t y = __funnelshift_r(ad[0], ad[1], sh);
-                        x ^= y;
-                        pm = (pm << 1) | (__popc(y) & 1u);
-                        ad += T;
-                    }
+                    for (uint32_t i = 0; i < n0; ++i, ad += T) take(__funnelshift_r(ad[0], ad[1], sh), pm0);
+#pragma unroll 4
+                    for (uint32_t i = 0; i < n1; ++i, ad += T) take(__funnelshift_r(ad[0], ad[1], sh), pm1);
                     if (tl == tl_last) lo = ad[0];
                 }
                 if (tl == tl_last) {  // the last word holds positions up to n only
                     const uint32_t y = __funnelshift_r(lo, ad[1], sh) & a.ylast;
-                    x ^= y;
-                    pm = (pm << 1) | (__popc(y) & 1u);
+                    if (cnt < 32u)
+                        take(y, pm0);
+                    else
+                        take(y, pm1);
                     ++cnt;
                 }
-                pm = cnt ? __brev(pm) >> (32u - cnt) : 0u;
+                const uint32_t m0 = min(cnt, 32u), m1 = cnt - m0;
+                pm0 = m0 ? __brev(pm0) >> (32u - m0) : 0u;
+                if (wide) pm1 = m1 ? __brev(pm1) >> (32u - m1) : 0u;
             }
-            uint32_t h = ((__popc(pm) & 1u) ? tl : 0u) ^ (fold5(pm) << tlog);
+            // indices i of the odd-parity words (those of pm1 are 32 + their bit index;
+            // pm1 is used only when a lane reads more than 32 words)
+            uint32_t fi = fold5(pm0), par = __popc(pm0);
+            if (wide) {
+                const uint32_t par1 = __popc(pm1) & 1u;
+                fi ^= fold5(pm1) ^ (par1 << 5);
+                par ^= par1;
+            }
+            uint32_t h = ((par & 1u) ? tl : 0u) ^ (fi << tlog);
             // XOR over the team: butterfly steps stay inside aligned groups of T lanes
             for (uint32_t o = T >> 1; o > 0; o >>= 1) {
                 x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
@@ -648,17 +668,21 @@ void remember_short_variant(uint32_t n, int v)
 }
 
 // Team size of the syndrome pass: a team of T lanes reads a codeword's Y
-// position-domain words, ceil(Y / T) per lane (at most 32: one bit each in the
-// parity mask), and pays a fixed cost per codeword for the reductions.  Pick
-// the T with the fewest lane instructions per tile by a simple cost model.
+// position-domain words, ceil(Y / T) per lane (at most 64: one bit each in the
+// two parity masks), and a tile's codewords take ceil(g / (32 / T)) rounds.
+// Each round ends in a chain of dependent steps (the reductions, the
+// butterfly over the team, the correction), which on GB300 measured as long as
+// about 31 word steps (the paper's (M, t) grid: 3 rounds of 13 words took 139
+// µs where 1 round of 32 took 111), plus a little per butterfly step.  Pick
+// the T with the lowest cost per tile.
 uint32_t team_log(uint32_t Y, uint32_t g)
 {
     uint32_t best = 5;
     uint64_t best_cost = ~0ull;
     for (uint32_t lg = 0; lg <= 5; ++lg) {
         const uint32_t T = 1u << lg, G = 32u >> lg, per_lane = (Y + T - 1) / T;
-        if (per_lane > 32) continue;
-        const uint64_t cost = (uint64_t)((g + G - 1) / G) * 32u * (per_lane * 10u + 35u);
+        if (per_lane > 64) continue;
+        const uint64_t cost = (uint64_t)((g + G - 1) / G) * (per_lane * 10u + 310u + 30u * lg);
         if (cost < best_cost) {
             best_cost = cost;
             best = lg;
