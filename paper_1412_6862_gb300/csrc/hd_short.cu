@@ -584,12 +584,28 @@ ShortVariant make_short_variant()
 }
 
 const ShortVariant kShortVariants[] = {
-    make_short_variant<8, 2, 4096>(),  // the built-in choice: fastest over the paper's (M, t) grid on GB300
+    // the built-in choice: fastest over the paper's (M, t) grid on GB300 (the
+    // kernel waits on fixed-latency chains, so warps per SM count: two of these
+    // CTAs hold 24 warps, two 8-warp CTAs of 4 KB stages only 16)
+    make_short_variant<12, 2, 4096>(),
+    make_short_variant<8, 2, 4096>(),
     make_short_variant<4, 2, 8192>(),
     make_short_variant<4, 3, 4096>(),
     make_short_variant<4, 4, 2048>(),
+    make_short_variant<16, 2, 2048>(),
+    make_short_variant<16, 2, 3072>(),
 };
 constexpr int kNumShortVariants = sizeof(kShortVariants) / sizeof(kShortVariants[0]);
+
+// The configuration with the largest stages (the first of them), which holds a
+// codeword of every supported length.
+int largest_stage_variant()
+{
+    int best = 0;
+    for (int v = 1; v < kNumShortVariants; ++v)
+        if (kShortVariants[v].SB > kShortVariants[best].SB) best = v;
+    return best;
+}
 constexpr uint32_t kTabSmemMax = 40u << 10;  // larger tables stay in global memory
 
 std::mutex g_short_mu;
@@ -849,11 +865,7 @@ cudaError_t launch_short_tiles(int vi, const uint32_t *in, uint32_t n, uint64_t 
     a.bulk_end = (a.in_words * 4) >> 4 << 4;
     a.n = n;
     a.k = k;
-    switch (v.SB) {
-        case 8192: a.g = tile_codewords<8192>(n); break;
-        case 4096: a.g = tile_codewords<4096>(n); break;
-        default: a.g = tile_codewords<2048>(n); break;
-    }
+    a.g = std::min<uint32_t>((8u * v.SB - 256u) / n, TileGeom<4096>::max_g);  // as tile_codewords<SB>
     if (a.g == 0) return cudaErrorInvalidValue;  // the caller picks a configuration whose stage holds a codeword
     a.ntiles = (num_cw + a.g - 1) / a.g;
     a.Y = (n + 32) / 32;
@@ -945,7 +957,7 @@ hd_status decode_short_with(const uint32_t *stream, uint64_t in_bits, uint32_t n
     const int syn = syndromes ? (int)syn_type : 0;
     if (k >= kLongMinK) {
         int vi = current_short_variant(n);
-        if (kShortVariants[vi].SB * 8u < n + 256u) vi = 1;  // stage too small for one codeword: largest stage
+        if (kShortVariants[vi].SB * 8u < n + 256u) vi = largest_stage_variant();  // stage too small for a codeword
         if (launch_short_tiles(vi, stream, n, num_codewords, out_bits, syndromes, syn, err_count, detected_count,
                                st, table, tab_len, pdl) != cudaSuccess)
             return HD_ERR_CUDA;

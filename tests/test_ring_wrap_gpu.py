@@ -206,7 +206,7 @@ def test_stream_group_configuration_wraps_its_rings():
 
 @pytest.mark.parametrize("n", [545, 2679, 8013, 32767])
 def test_shortened_configurations_wrap_their_rings(n):
-    """Every tiled shortened-code configuration on two CTAs (warps <= 8,
+    """Every tiled shortened-code configuration on two CTAs (warps <= 16,
     stages <= 4, stages of at most 8 KB: 4 MB of input gives every warp more
     than 30 tiles); the lengths cover the three table placements (split
     tables for k < 1280, the table in shared memory, in global memory)."""
