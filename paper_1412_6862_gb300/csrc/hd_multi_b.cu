@@ -6,7 +6,7 @@ namespace hd {
 
 void register_multi_b(std::vector<MultiVariant> &v)
 {
-    add_multi_variants<63, 128, 3, 32, 1>(v);
+    add_multi_variants<63, 64, 2, 32, 1>(v);
     add_multi_variants<127, 256, 3, 8, 1>(v);
     add_multi_variants<255, 128, 2, 8, 1>(v);
 }
