@@ -82,6 +82,7 @@ struct MultiCfg {
     static_assert(off_in % 16 == 0 && stage_bytes % 16 == 0 && out_buf_bytes % 16 == 0, "bulk copy alignment");
     static_assert(!LUT || N_ == 7 || N_ == 15, "decode tables exist for n = 7 and 15");
     static_assert(chunk_cw <= (1u << (32 - kTailShift)), "a tail's count fits its field");
+    static_assert(Q::ALIGNED || Q::GK % 8 == 0, "a part's unaligned output ends are written bytewise: whole bytes");
 };
 
 // A 4-byte asynchronous copy into shared memory, and an arrive on `bar` once

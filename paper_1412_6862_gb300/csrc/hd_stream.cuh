@@ -57,7 +57,6 @@ struct ChunkGeom {
     static constexpr bool WIDE = (SB == 1 && C::m + (XH ? 1 : 0) >= 8);
     static constexpr int GK = G * C::k;                               // output bits per thread
     static constexpr bool ALIGNED = (H == 1) || (GK % 32 == 0);
-    static_assert(ALIGNED || GK % 8 == 0, "an unaligned part's ends are written bytewise: whole bytes");
     static constexpr int R = (G * L + 31) / 32;                       // input words per thread after re-alignment
     static constexpr uint32_t in_words = TEAMS * L;
     static constexpr uint32_t in_bytes = in_words * 4;
