@@ -12,7 +12,7 @@ void register_multi_a(std::vector<MultiVariant> &v)
     add_multi_variants<7, 128, 4, 32, 1>(v);
     add_multi_variants<15, 576, 2, 32, 0, true>(v);
     add_multi_variants<15, 256, 4, 32, 1>(v);
-    add_multi_variants<31, 128, 3, 32, 1>(v);
+    add_multi_variants<31, 128, 2, 32, 1>(v);
 }
 
 }  // namespace hd
